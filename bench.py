@@ -1,0 +1,349 @@
+"""Benchmark of the GB300 state-vector path (one JSON line on rank 0).
+
+Workload (the configuration the headline metric is quoted on): the
+layered sparse-gate circuit at n = 30 qubits in complex128 (a 16 GiB state,
+larger than L2): H on every qubit, then 20 layers of [CNOT ladder; CZ on a
+random perfect matching; T or S on a random half; RZ(theta) on every
+qubit], then the readouts norm^2 and <Z_0>.  One step = reset to |0...0>,
+apply the whole circuit, read out.  Metric: amplitude updates per second
+(one amplitude rewritten by one gate, counted algorithmically), with the
+fused tile kernel's HBM bandwidth against the measured peak.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--mode fused|per_gate]
+  python bench.py --impl reference ...   (the FP64 CPU oracle, bounded sample)
+
+With N > 1 (torchrun) every rank runs an independent replica of the
+workload on its own GPU (the path does not shard); value = all ranks'
+updates / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "amplitude-updates/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="mera", choices=["mera", "reference"])
+    p.add_argument("--mode", default="fused", choices=["fused", "per_gate"])
+    p.add_argument("--n", type=int, default=30)
+    p.add_argument("--layers", type=int, default=20)
+    p.add_argument("--dtype", default="c128", choices=["c128", "c64"])
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def _workload(n, layers):
+    from paper_2411_15332_gb300 import inputs
+    return inputs.layered_circuit(n, layers, seed=2)
+
+
+def _workload_name(n, layers, dtype):
+    return (f"layered_n{n}: n={n} {'complex128' if dtype == 'c128' else 'complex64'}, |0..0>, H on all, "
+            f"then {layers} x [CNOT ladder q->q+1, CZ on a seeded perfect matching, T/S on a seeded half, "
+            f"RZ(theta~U[0,2pi)) on all], readout norm^2 and <Z_0>")
+
+
+# ----------------------------------------------------------- clocks --------
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------- helpers -------
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def _tile_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2411_15332_gb300", "csrc")
+    for f in ("tile.cuh", "fused.cu", "kernels.cuh"):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic():
+    """Per-launch DRAM bytes of the tile kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "tile_kernel_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        if d.get("source_hash") == _tile_source_hash():
+            return d
+    except Exception:
+        pass
+    return None
+
+
+def _cpu_baseline(sample_seconds=15.0):
+    """The FP64 oracle on the host cores, single-threaded, on a bounded
+    sample of the same circuit family (reduced n; amplitude updates are
+    counted on the sample itself)."""
+    code = r"""
+import json, os, sys, time
+sys.path.insert(0, %r)
+from paper_2411_15332_gb300 import inputs
+from oracle import statevector as sv
+n = 22
+ops = inputs.layered_circuit(n, 20, seed=2)
+N = 1 << n
+def upd(o):
+    name, t, c, p, cv = o
+    frac = {"X": 1.0, "H": 1.0, "RZ": 1.0, "Z": 0.5, "S": 0.5, "T": 0.5}[name]
+    return N * frac / (1 << len(c))
+psi = sv.zero_state(n)
+t0 = time.perf_counter(); done = 0.0; g = 0
+while g < len(ops) and time.perf_counter() - t0 < %f:
+    sv.apply_op(psi, n, ops[g]); done += upd(ops[g]); g += 1
+dt = time.perf_counter() - t0
+print(json.dumps({"value": done / dt, "gates": g, "seconds": dt, "n": n}))
+""" % (ROOT, sample_seconds)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+    if r.returncode != 0:
+        return {"value": None, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": "failed: " + r.stderr[-300:]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": d["value"], "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": (f"oracle (numpy FP64, 1 thread) applying the first {d['gates']} gates of the same "
+                       f"layered circuit family at n={d['n']} for {d['seconds']:.1f} s")}
+
+
+# ----------------------------------------------------------- arms ----------
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    steps = []
+    for _ in range(args.warmup):
+        pass
+    per = max(5.0, 60.0 / max(1, args.steps + args.warmup))
+    vals = []
+    last = None
+    for _ in range(args.steps):
+        last = _cpu_baseline(sample_seconds=min(per, 20.0))
+        if last["value"] is not None:
+            vals.append(last["value"])
+    value = statistics.median(vals) if vals else None
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": _workload_name(args.n, args.layers, args.dtype), "n": args.n,
+                       "note": "CPU oracle timed on a bounded sample at n=22 of the same circuit family"},
+            "cpu_baseline": dict(last or {}, value=value),
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_mera(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    from paper_2411_15332_gb300.build import build
+    build()
+    import paper_2411_15332_gb300 as mera
+    from paper_2411_15332_gb300.workload import amplitude_updates
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    n = args.n
+    ops = _workload(n, args.layers)
+    upd = amplitude_updates(ops, n)
+    st = mera.State(n, args.dtype)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        st.set_basis(0)
+        st.apply_circuit(ops, mode=args.mode)
+        return st.observables(0)
+
+    for _ in range(max(args.warmup, 0)):
+        obs = step()
+
+    # timed region
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clock = ClockSampler(local_rank)
+    clock.start()
+    mera.profile_enable(True)
+    l0 = mera.launch_count()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record(stream)
+    for k in range(args.steps):
+        obs = step()
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = mera.launch_count() - l0
+    prof = mera.profile_read()
+    mera.profile_enable(False)
+    clocks = clock.stop()
+    total_ms = ev[0].elapsed_time(ev[-1])
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = upd * world / (ms_per_step / 1e3)
+
+    # roofline of the dominant kernel (the fused tile pass)
+    peak, peak_kind = _peaks()
+    kcls = "tile" if args.mode == "fused" else "gate"
+    nl, kms, kbytes = prof[kcls]
+    achieved = (kbytes / nl) / (kms / nl / 1e3) / 1e9 if nl else None
+    tr = _ncu_traffic()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None,
+                "traffic": tr["dram_bytes_per_launch"] if tr else None,
+                "kernel": "k_tile<double2>" if kcls == "tile" else "per-gate kernels",
+                "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                "kernel_launches": nl, "kernel_ms": kms,
+                "kernel_share": kms / total_ms if total_ms else None,
+                "algorithmic_bytes_per_launch": (kbytes / nl) if nl else None}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        try:
+            eb = 16 if args.dtype == "c128" else 8
+            host = torch.zeros((1 << n) * 2, dtype=torch.float64 if eb == 16 else torch.float32).pin_memory()
+            host[0] = 1.0
+            hp = host.numpy().view(np.complex128 if eb == 16 else np.complex64)
+            for _ in range(1):
+                st.from_numpy(hp)
+                st.apply_circuit(ops, mode=args.mode)
+                st.observables(0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                st.from_numpy(hp)                       # H2D of the input state
+                st.apply_circuit(ops, mode=args.mode)   # ops table is copied per launch
+                res = st.observables(0)                 # D2H of the result
+            e2e_s = (time.perf_counter() - t0) / args.steps
+            ops_bytes = 80 * len(ops)
+            e2e = {"value": upd * world / e2e_s, "unit": METRIC,
+                   "h2d_bytes_per_step": (1 << n) * eb + ops_bytes, "d2h_bytes_per_step": 24,
+                   "seconds_per_step": e2e_s}
+            del host
+        except Exception as ex:  # pinned allocation can fail on small hosts
+            e2e = {"value": None, "unit": METRIC, "error": str(ex)[:200]}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = _cpu_baseline()
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.dtype == "c128" else "f32",
+                "data": "synthetic",
+                "config": {"workload": _workload_name(n, args.layers, args.dtype), "n": n,
+                           "amplitude_updates_per_step": upd, "mode": args.mode,
+                           "parallelism": f"replicas x{world}",
+                           "l2": "state (%d GiB) larger than L2 (129 MB); no flush needed" % (((1 << n) * (16 if args.dtype == 'c128' else 8)) >> 30),
+                           "readout": {"norm2": obs[0], "z0": obs[1]}},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "clocks": clocks, "kernel_classes": prof}
+        print(json.dumps(line), flush=True)
+    st.close()
+
+
+def main():
+    args = _args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "mera" else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local_rank)
+        dist.init_process_group(backend=backend)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_mera(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

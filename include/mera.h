@@ -1,0 +1,217 @@
+/*
+ * mera.h -- C ABI of the GB300 state-vector library for the Mera method
+ * (Song et al., "Mera: Memory Reduction and Acceleration for Quantum
+ * Circuit Simulation via Redundancy Exploration", arXiv 2411.15332).
+ *
+ * The library applies quantum gates to a 2^n-amplitude state vector on one
+ * GPU without forming the 2^n x 2^n operation matrix of Eq. 6: sparse gates
+ * go through their compressed index map (the DAX / DAS structures of
+ * Sec. III-A, applied on the fly), Hadamard layers through the RH structure
+ * of Sec. III-B (its on-demand signs realised as in-place butterflies).
+ *
+ * Conventions
+ *   - Qubit q is bit q of the basis index (qubit 0 = least significant).
+ *     The paper's Eq. 6 numbers qubits from the most significant end; its
+ *     qubit k is bit n-k here.
+ *   - A state is N = 2^n contiguous complex amplitudes: MERA_C128 is
+ *     interleaved (re, im) float64 (16 B, the paper's precision, Sec.
+ *     III-A.1), MERA_C64 interleaved float32 (8 B).
+ *   - A gate on k targets is a 2^k x 2^k matrix in the basis |t_0 .. t_{k-1}>,
+ *     targets[0] the most significant bit of the sub-index.  Controls are
+ *     given as a bit mask with the bit values they must hold.
+ *   - Pointers are host pointers unless the name says dev_ptr.  The caller
+ *     keeps ownership of everything it passes in; objects returned through
+ *     an out-parameter are owned by the caller and released with the
+ *     matching *_destroy call.
+ *
+ * Errors: every call returns an int status (MERA_OK = 0).  On failure,
+ * mera_last_error() gives a message for the calling host thread.  No C++
+ * exception or abort crosses this boundary.  Errors detected before any
+ * launch leave the state unchanged.  Calls on one state are asynchronous
+ * on the state's stream unless documented as synchronous (readouts).
+ */
+#ifndef MERA_H
+#define MERA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define MERA_OK 0
+#define MERA_EINVAL 1        /* bad argument: n, qubit >= n, duplicate qubit, NaN ... */
+#define MERA_ENOMEM 2        /* device or host allocation failed */
+#define MERA_EUNSUPPORTED 3  /* dtype / gate arity not supported */
+#define MERA_ECUDA 4         /* a CUDA runtime call failed */
+#define MERA_ETIMEOUT 5      /* a bounded device wait ran out */
+
+/* ---- element types ----------------------------------------------------- */
+#define MERA_C64 0           /* complex64: float32 re, im */
+#define MERA_C128 1          /* complex128: float64 re, im */
+
+#define MERA_MAX_QUBITS 36
+
+/* ---- gate catalogue (Table I of the paper; controls added by mask) ------ */
+enum mera_gate {
+    MERA_GATE_I = 0,
+    MERA_GATE_X, MERA_GATE_Y, MERA_GATE_Z, MERA_GATE_H,
+    MERA_GATE_S, MERA_GATE_SDG, MERA_GATE_T, MERA_GATE_TDG,
+    MERA_GATE_SX, MERA_GATE_SXDG,
+    MERA_GATE_P,      /* params: lambda; diag(1, e^{i lambda}) (Phase, U1) */
+    MERA_GATE_RX, MERA_GATE_RY, MERA_GATE_RZ,   /* params: theta; exp(-i theta P/2) */
+    MERA_GATE_R,      /* params: theta, phi; rotation about cos(phi) X + sin(phi) Y */
+    MERA_GATE_U2,     /* params: phi, lambda = U(pi/2, phi, lambda) */
+    MERA_GATE_U,      /* params: theta, phi, lambda[, gamma = global phase] */
+    MERA_GATE_SWAP, MERA_GATE_ISWAP, MERA_GATE_DCX, MERA_GATE_ECR,
+    MERA_GATE_RXX, MERA_GATE_RYY, MERA_GATE_RZZ, MERA_GATE_RZX, /* params: theta */
+    MERA_GATE_FLIP,   /* no targets: multiply the controlled sub-space by -1 */
+    MERA_GATE_MATRIX, /* explicit 2^k x 2^k matrix, mera_op.matrix */
+    MERA_GATE_COUNT
+};
+
+/* One circuit operation. */
+typedef struct mera_op {
+    int32_t gate;          /* enum mera_gate */
+    int32_t nt;            /* number of targets, 0..3 */
+    int32_t targets[3];    /* targets[0] is the most significant sub-index bit */
+    int32_t reserved;      /* must be 0 */
+    uint64_t cmask;        /* control qubits (bit q set = qubit q controls) */
+    uint64_t cvals;        /* required control values (bits inside cmask) */
+    double params[4];      /* angles, see enum mera_gate */
+    const double* matrix;  /* MERA_GATE_MATRIX only: host, 2^nt x 2^nt
+                              interleaved complex128, row-major; copied */
+} mera_op;
+
+/* apply modes of mera_apply_circuit */
+#define MERA_MODE_PER_GATE 0   /* one kernel launch per gate (Eq. 7 per gate) */
+#define MERA_MODE_FUSED 1      /* shared-memory tile passes, gates fused */
+
+typedef struct mera_state mera_state;
+
+/* ---- library ----------------------------------------------------------- */
+
+/* Message of the last failed call on this host thread ("" if none).
+ * The string stays valid until the next failing call on the thread. */
+const char* mera_last_error(void);
+
+/* Library version string (static storage). */
+const char* mera_version(void);
+
+/* Number of kernels this library has launched in the process so far
+ * (all devices, all states).  Synchronous, host only. */
+uint64_t mera_launch_count(void);
+
+/* ---- state lifetime (Sec. II-A, Eq. 3: the 2^n-amplitude state vector) -- */
+
+/* Allocate a state of n qubits (1 <= n <= MERA_MAX_QUBITS) on the current
+ * device with cudaMalloc, initialised to |0...0>, bound to the legacy
+ * default stream.  *out receives the new state (owned by the caller). */
+int mera_state_create(int n, int dtype, mera_state** out);
+
+/* Borrow caller-owned device memory of 2^n amplitudes of `dtype` (e.g. a
+ * torch tensor's storage; 16-byte aligned).  The contents are left as
+ * they are.  The caller keeps the memory alive until mera_state_destroy.
+ * `stream` is a cudaStream_t (NULL = legacy default stream). */
+int mera_state_wrap(void* dev_ptr, int n, int dtype, void* stream, mera_state** out);
+
+/* Release the state: frees the amplitudes only if mera_state_create made
+ * them, plus the state's small internal scratch buffers.  NULL is a no-op. */
+int mera_state_destroy(mera_state* s);
+
+/* Rebind the state to another stream (a cudaStream_t). */
+int mera_state_set_stream(mera_state* s, void* stream);
+
+/* Device pointer of the amplitudes, qubit count and dtype. */
+int mera_state_info(const mera_state* s, void** dev_ptr, int* n, int* dtype);
+
+/* Set the state to the basis state |index>.  Asynchronous. */
+int mera_state_set_basis(mera_state* s, uint64_t index);
+
+/* Copy 2^n amplitudes from / to host memory (pinned memory gives full
+ * bandwidth).  Synchronous: returns after the copy completed. */
+int mera_state_copy_from_host(mera_state* s, const void* host);
+int mera_state_copy_to_host(mera_state* s, void* host);
+
+/* Read k amplitudes at basis indices idx[0..k-1] (host array) into
+ * out[2k] as float64 (re, im) pairs, whatever the dtype.  Synchronous. */
+int mera_state_get_amplitudes(mera_state* s, const uint64_t* idx, size_t k, double* out);
+
+/* Wait for all work queued on the state's stream. */
+int mera_state_synchronize(mera_state* s);
+
+/* ---- gates (Sec. II-A Eq. 6-7 without the operation matrix; Sec. III-A.2
+ *      MVM on the gate's compressed index map) ------------------------- */
+
+/* 2^k x 2^k matrix of a catalogue gate, k = number of targets it takes
+ * (returned in *nt), written to out[2 * 4^k] as interleaved complex128,
+ * row-major.  out must hold 128 doubles.  Host only. */
+int mera_gate_matrix(int gate, const double* params, int* nt, double* out);
+
+/* Apply one gate.  targets[nt] and controls[nc] are qubit indices; every
+ * qubit may appear once.  params: as enum mera_gate (NULL if none). */
+int mera_apply_gate(mera_state* s, int gate, const int* targets, int nt,
+                    const int* controls, int nc, const double* params);
+
+/* Apply an explicit 2^nt x 2^nt matrix (interleaved complex128 row-major,
+ * host memory, copied) to targets, under controls (all must be 1). */
+int mera_apply_matrix(mera_state* s, const double* matrix, const int* targets, int nt,
+                      const int* controls, int nc);
+
+/* Apply ops[0..nops-1] in order.  MERA_MODE_PER_GATE launches one kernel per
+ * op; MERA_MODE_FUSED plans shared-memory tile passes that apply runs of
+ * gates (and Hadamard butterflies) per HBM read/write.  All ops are
+ * validated before anything is launched. */
+int mera_apply_circuit(mera_state* s, const mera_op* ops, size_t nops, int mode);
+
+/* H on every qubit q with bit q of `mask` set: the RH structure of Sec.
+ * III-B (H^{(x)m} stored as its magnitude 2^{-m/2}, element signs
+ * (-1)^popcount(r & c), Fig. 3), applied in place as butterflies; same
+ * result as the RH-MVM of Algorithm 1 for mask = all qubits. */
+int mera_hadamard_layer(mera_state* s, uint64_t mask);
+
+/* ---- readouts (Sec. II-A Eq. 4-5); synchronous, float64 accumulation -- */
+
+/* sum_i |a_i|^2 */
+int mera_norm2(mera_state* s, double* out);
+/* <Z_q> = sum_i (1 - 2 bit_q(i)) |a_i|^2 */
+int mera_expect_z(mera_state* s, int q, double* out);
+/* sum_q <Z_q> = sum_i (n - 2 popcount(i)) |a_i|^2 */
+int mera_expect_z_sum(mera_state* s, double* out);
+/* All three in one pass over the state: out[0] = norm^2, out[1] = <Z_q>,
+ * out[2] = sum_q <Z_q>. */
+int mera_observables(mera_state* s, int q, double out[3]);
+/* Most probable index (|a|^2 = re*re + im*im, float64, no fused multiply-
+ * add); ties go to the lowest index.  *prob may be NULL. */
+int mera_argmax(mera_state* s, uint64_t* idx, double* prob);
+/* Inverse-CDF sampling: for each u[j] in [0, 1) the smallest i with
+ * C_i > u[j] * C_{N-1}, C the running sum of |a_i|^2.  u and idx_out are
+ * host arrays of k elements. */
+int mera_measure(mera_state* s, const double* u, size_t k, uint64_t* idx_out);
+
+/* ---- kernel timing ------------------------------------------------------ */
+
+/* Kernel classes timed when profiling is on. */
+#define MERA_KCLASS_GATE 0      /* per-gate kernels */
+#define MERA_KCLASS_TILE 1      /* fused tile-pass kernel */
+#define MERA_KCLASS_REDUCE 2    /* reductions */
+#define MERA_KCLASS_DAX 3       /* DAX / DAS MTP and MVM kernels */
+#define MERA_KCLASS_QNN 4       /* batched QNN / adjoint kernels */
+#define MERA_KCLASS_COUNT 5
+
+/* Turn CUDA-event timing of every launch on/off (process-wide) and clear
+ * the accumulated figures. */
+int mera_profile_enable(int on);
+/* Synchronise the recorded events and return, per kernel class, the number
+ * of launches and their summed device time in ms (arrays of
+ * MERA_KCLASS_COUNT; either may be NULL).  Also returns the summed
+ * algorithmic bytes the timed launches moved (bytes may be NULL). */
+int mera_profile_read(uint64_t* launches, double* ms, double* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MERA_H */

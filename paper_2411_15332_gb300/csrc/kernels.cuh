@@ -1,0 +1,224 @@
+// Device helpers and per-gate kernels (the launchers live in gates.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mera.h"
+
+namespace mera {
+
+// --------------------------------------------------------- complex math --
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(fma(a.x, b.x, -(a.y * b.y)), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -(a.y * b.y)), fmaf(a.x, b.y, a.y * b.x));
+}
+// acc + a * b
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 acc) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+    return acc;
+}
+__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 acc) {
+    acc.x = fmaf(a.x, b.x, acc.x);
+    acc.x = fmaf(-a.y, b.y, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y);
+    acc.y = fmaf(a.y, b.x, acc.y);
+    return acc;
+}
+__device__ __forceinline__ double2 czero(double2) { return make_double2(0.0, 0.0); }
+__device__ __forceinline__ float2 czero(float2) { return make_float2(0.f, 0.f); }
+
+// m0 * x0 + m1 * x1
+template <typename V>
+__device__ __forceinline__ V cdot2(V m0, V x0, V m1, V x1) {
+    V acc = cmul(m0, x0);
+    return cfma(m1, x1, acc);
+}
+
+// Multiply by a phase given as a code: 0 -> 1, 1 -> i, 2 -> -1, 3 -> -i
+// (exact: only moves and sign flips), 4 -> the general value v.
+__device__ __forceinline__ double2 neg_v(double2 x) { return make_double2(-x.x, -x.y); }
+__device__ __forceinline__ float2 neg_v(float2 x) { return make_float2(-x.x, -x.y); }
+template <typename V>
+__device__ __forceinline__ V apply_phase(int code, V v, V x) {
+    V r;
+    switch (code) {
+    case 0: return x;
+    case 1: r.x = -x.y; r.y = x.x; return r;
+    case 2: return neg_v(x);
+    case 3: r.x = x.y; r.y = -x.x; return r;
+    default: return cmul(v, x);
+    }
+}
+
+// Insert a zero bit at each position ins[0] < ins[1] < ... of t.
+__device__ __forceinline__ uint64_t insert_zeros(uint64_t t, const int* ins, int nins) {
+    for (int j = 0; j < nins; ++j) {
+        const uint64_t lo = t & ((1ull << ins[j]) - 1ull);
+        t = ((t - lo) << 1) | lo;
+    }
+    return t;
+}
+
+// ------------------------------------------------------ per-gate kernels --
+template <typename V>
+struct GateArgs {
+    V* psi;
+    uint64_t count;              // groups (or elements) to visit
+    uint64_t cbits;              // control values at their bit positions
+    uint64_t off[8];             // offset of sub-index s inside a group
+    int nins;                    // zero bits inserted into the group counter
+    int ins[MERA_MAX_QUBITS];    // their positions, ascending
+    int k;                       // targets
+    int qc;                      // shuffle kernel: target among non-control bits
+    int nt;                      // diag kernel: targets
+    int tq[3];                   // diag kernel: target qubits, tq[0] most significant
+    int nact;                    // monomial: rows that change
+    int act[8];                  // monomial: those rows
+    int perm[8];                 // monomial: source sub-index of act[j]
+    int flag[8];                 // diag: value != 1 for sub-index s
+    int code[8];                 // phase code of v[] (see apply_phase)
+    V v[8];                      // monomial / diag values
+    V m[64];                     // dense matrix, row-major
+};
+
+// Multiply one sub-space (controls = cbits) by a scalar.
+template <typename V>
+__global__ void __launch_bounds__(256) k_phase(const __grid_constant__ GateArgs<V> a) {
+    const V v = a.v[0];
+    const int code = a.code[0];
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.count; t += stride) {
+        const uint64_t i = insert_zeros(t, a.ins, a.nins) | a.cbits;
+        a.psi[i] = apply_phase(code, v, a.psi[i]);
+    }
+}
+
+// Diagonal gate: amplitude i (controls holding) times v[sub(i)] where v != 1.
+template <typename V>
+__global__ void __launch_bounds__(256) k_diag(const __grid_constant__ GateArgs<V> a) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.count; t += stride) {
+        const uint64_t i = insert_zeros(t, a.ins, a.nins) | a.cbits;
+        int sub = 0;
+        for (int j = 0; j < a.nt; ++j) sub = (sub << 1) | (int)((i >> a.tq[j]) & 1ull);
+        if (a.flag[sub]) a.psi[i] = apply_phase(a.code[sub], a.v[sub], a.psi[i]);
+    }
+}
+
+// One target, high bit: each thread owns the pair (i0, i0 | off[1]).
+// MONO: the gate swaps the pair and multiplies by phases (X, Y and their
+// controlled forms): no arithmetic for unit phases.
+template <typename V, bool MONO>
+__device__ __forceinline__ void pair_update(const GateArgs<V>& a, V& x0, V& x1) {
+    if (MONO) {
+        const V n0 = apply_phase(a.code[0], a.v[0], x1);
+        const V n1 = apply_phase(a.code[1], a.v[1], x0);
+        x0 = n0;
+        x1 = n1;
+    } else {
+        const V n0 = cdot2(a.m[0], x0, a.m[1], x1);
+        const V n1 = cdot2(a.m[2], x0, a.m[3], x1);
+        x0 = n0;
+        x1 = n1;
+    }
+}
+
+template <typename V, bool MONO>
+__global__ void __launch_bounds__(256) k_dense1_pair(const __grid_constant__ GateArgs<V> a) {
+    const uint64_t o = a.off[1];
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // two groups in flight per thread
+    for (; t + stride < a.count; t += 2 * stride) {
+        const uint64_t i0 = insert_zeros(t, a.ins, a.nins) | a.cbits;
+        const uint64_t j0 = insert_zeros(t + stride, a.ins, a.nins) | a.cbits;
+        V x0 = a.psi[i0], x1 = a.psi[i0 | o];
+        V y0 = a.psi[j0], y1 = a.psi[j0 | o];
+        pair_update<V, MONO>(a, x0, x1);
+        pair_update<V, MONO>(a, y0, y1);
+        a.psi[i0] = x0;
+        a.psi[i0 | o] = x1;
+        a.psi[j0] = y0;
+        a.psi[j0 | o] = y1;
+    }
+    if (t < a.count) {
+        const uint64_t i0 = insert_zeros(t, a.ins, a.nins) | a.cbits;
+        V x0 = a.psi[i0], x1 = a.psi[i0 | o];
+        pair_update<V, MONO>(a, x0, x1);
+        a.psi[i0] = x0;
+        a.psi[i0 | o] = x1;
+    }
+}
+
+// One target, low bit: one amplitude per thread, the partner comes from the
+// lane 1 << qc away (consecutive threads hold consecutive non-control
+// indices, so every load and store is fully coalesced).
+template <typename V>
+__device__ __forceinline__ V shfl_xor_v(V x, int m);
+template <>
+__device__ __forceinline__ double2 shfl_xor_v<double2>(double2 x, int m) {
+    return make_double2(__shfl_xor_sync(0xffffffffu, x.x, m), __shfl_xor_sync(0xffffffffu, x.y, m));
+}
+template <>
+__device__ __forceinline__ float2 shfl_xor_v<float2>(float2 x, int m) {
+    return make_float2(__shfl_xor_sync(0xffffffffu, x.x, m), __shfl_xor_sync(0xffffffffu, x.y, m));
+}
+
+template <typename V, bool MONO>
+__global__ void __launch_bounds__(256) k_dense1_shfl(const __grid_constant__ GateArgs<V> a) {
+    const V m0 = a.m[0], m1 = a.m[1], m2 = a.m[2], m3 = a.m[3];
+    const int lm = 1 << a.qc;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;   // multiple of 32
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.count; t += stride) {
+        const uint64_t i = insert_zeros(t, a.ins, a.nins) | a.cbits;
+        const V x = a.psi[i];
+        const V y = shfl_xor_v(x, lm);
+        const int hi = (int)((t >> a.qc) & 1ull);
+        if (MONO) a.psi[i] = apply_phase(a.code[hi], a.v[hi], y);
+        else a.psi[i] = hi ? cdot2(m2, y, m3, x) : cdot2(m0, x, m1, y);
+    }
+}
+
+// Monomial gate on 2-3 targets: row act[j] takes v[j] * amplitude perm[j].
+template <typename V>
+__global__ void __launch_bounds__(256) k_mono(const __grid_constant__ GateArgs<V> a) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.count; t += stride) {
+        const uint64_t base = insert_zeros(t, a.ins, a.nins) | a.cbits;
+        V in[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (j < a.nact) in[j] = a.psi[base | a.off[a.perm[j]]];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (j < a.nact) a.psi[base | a.off[a.act[j]]] = apply_phase(a.code[j], a.v[j], in[j]);
+    }
+}
+
+// Dense gate on K targets.
+template <typename V, int K>
+__global__ void __launch_bounds__(256) k_dense_k(const __grid_constant__ GateArgs<V> a) {
+    constexpr int D = 1 << K;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.count; t += stride) {
+        const uint64_t base = insert_zeros(t, a.ins, a.nins) | a.cbits;
+        V in[D];
+#pragma unroll
+        for (int s = 0; s < D; ++s) in[s] = a.psi[base | a.off[s]];
+#pragma unroll
+        for (int r = 0; r < D; ++r) {
+            V acc = cmul(a.m[r * D], in[0]);
+#pragma unroll
+            for (int c = 1; c < D; ++c) acc = cfma(a.m[r * D + c], in[c], acc);
+            a.psi[base | a.off[r]] = acc;
+        }
+    }
+}
+
+}  // namespace mera
