@@ -43,7 +43,8 @@ def _args():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="mera", choices=["mera", "reference"])
     p.add_argument("--mode", default="fused", choices=["fused", "per_gate"])
-    p.add_argument("--n", type=int, default=30)
+    p.add_argument("--workload", default="layered", choices=["layered", "grover"])
+    p.add_argument("--n", type=int, default=None)
     p.add_argument("--layers", type=int, default=20)
     p.add_argument("--dtype", default="c128", choices=["c128", "c64"])
     p.add_argument("--no-e2e", action="store_true")
@@ -51,14 +52,21 @@ def _args():
     return p.parse_args()
 
 
-def _workload(n, layers):
+def _workload(args):
     from paper_2411_15332_gb300 import inputs
-    return inputs.layered_circuit(n, layers, seed=2)
+    if args.workload == "grover":
+        ops, _m = inputs.grover_circuit(args.n, 8, seed=3)
+        return ops
+    return inputs.layered_circuit(args.n, args.layers, seed=2)
 
 
-def _workload_name(n, layers, dtype):
-    return (f"layered_n{n}: n={n} {'complex128' if dtype == 'c128' else 'complex64'}, |0..0>, H on all, "
-            f"then {layers} x [CNOT ladder q->q+1, CZ on a seeded perfect matching, T/S on a seeded half, "
+def _workload_name(args):
+    n, dt = args.n, ("complex128" if args.dtype == "c128" else "complex64")
+    if args.workload == "grover":
+        return (f"grover_n{n}: n={n} {dt}, |0..0>, H on all, then 8 x [sign flip of a seeded index, H on all, "
+                f"sign flip of |0..0>, H on all], readout norm^2 and <Z_0>")
+    return (f"layered_n{n}: n={n} {dt}, |0..0>, H on all, "
+            f"then {args.layers} x [CNOT ladder q->q+1, CZ on a seeded perfect matching, T/S on a seeded half, "
             f"RZ(theta~U[0,2pi)) on all], readout norm^2 and <Z_0>")
 
 
@@ -200,7 +208,7 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": _workload_name(args.n, args.layers, args.dtype), "n": args.n,
+            "config": {"workload": _workload_name(args), "n": args.n,
                        "note": "CPU oracle timed on a bounded sample at n=22 of the same circuit family"},
             "cpu_baseline": dict(last or {}, value=value),
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -220,7 +228,7 @@ def run_mera(args, rank, world, local_rank):
     if world > 1:
         import torch.distributed as dist
     n = args.n
-    ops = _workload(n, args.layers)
+    ops = _workload(args)
     upd = amplitude_updates(ops, n)
     st = mera.State(n, args.dtype)
     stream = torch.cuda.current_stream()
@@ -312,7 +320,7 @@ def run_mera(args, rank, world, local_rank):
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.dtype == "c128" else "f32",
                 "data": "synthetic",
-                "config": {"workload": _workload_name(n, args.layers, args.dtype), "n": n,
+                "config": {"workload": _workload_name(args), "n": n,
                            "amplitude_updates_per_step": upd, "mode": args.mode,
                            "parallelism": f"replicas x{world}",
                            "l2": "state (%d GiB) larger than L2 (129 MB); no flush needed" % (((1 << n) * (16 if args.dtype == 'c128' else 8)) >> 30),
@@ -325,6 +333,8 @@ def run_mera(args, rank, world, local_rank):
 
 def main():
     args = _args()
+    if args.n is None:
+        args.n = 33 if args.workload == "grover" else 30
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

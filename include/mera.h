@@ -64,7 +64,7 @@ enum mera_gate {
     MERA_GATE_RX, MERA_GATE_RY, MERA_GATE_RZ,   /* params: theta; exp(-i theta P/2) */
     MERA_GATE_R,      /* params: theta, phi; rotation about cos(phi) X + sin(phi) Y */
     MERA_GATE_U2,     /* params: phi, lambda = U(pi/2, phi, lambda) */
-    MERA_GATE_U,      /* params: theta, phi, lambda[, gamma = global phase] */
+    MERA_GATE_U,      /* params: theta, phi, lambda, gamma (4 values; gamma = global phase, 0 for U3) */
     MERA_GATE_SWAP, MERA_GATE_ISWAP, MERA_GATE_DCX, MERA_GATE_ECR,
     MERA_GATE_RXX, MERA_GATE_RYY, MERA_GATE_RZZ, MERA_GATE_RZX, /* params: theta */
     MERA_GATE_FLIP,   /* no targets: multiply the controlled sub-space by -1 */
@@ -166,6 +166,13 @@ int mera_apply_matrix(mera_state* s, const double* matrix, const int* targets, i
  * validated before anything is launched. */
 int mera_apply_circuit(mera_state* s, const mera_op* ops, size_t nops, int mode);
 
+/* Describe how MERA_MODE_FUSED would run ops[0..nops-1] on n qubits of
+ * `dtype`, without touching a GPU: one line per tile pass (tile bits,
+ * arithmetic engine, Hadamard levels, register phases, op kinds), written
+ * as a NUL-terminated string into out[cap] (truncated if longer).  Host
+ * only; *npasses (may be NULL) receives the number of passes. */
+int mera_plan_summary(int n, int dtype, const mera_op* ops, size_t nops, char* out, size_t cap, int* npasses);
+
 /* H on every qubit q with bit q of `mask` set: the RH structure of Sec.
  * III-B (H^{(x)m} stored as its magnitude 2^{-m/2}, element signs
  * (-1)^popcount(r & c), Fig. 3), applied in place as butterflies; same
@@ -190,6 +197,53 @@ int mera_argmax(mera_state* s, uint64_t* idx, double* prob);
  * C_i > u[j] * C_{N-1}, C the running sum of |a_i|^2.  u and idx_out are
  * host arrays of k elements. */
 int mera_measure(mera_state* s, const double* u, size_t k, uint64_t* idx_out);
+
+/* ---- DAX / DAS compressed operation matrices (Sec. III-A) ---------------
+ *
+ * Device-resident, materialised forms of a 2^nq x 2^nq operation matrix:
+ *   DAX (Sec. III-A.1, Fig. 1a): per non-zero a float64 (re, im) value and
+ *       its row-major linear index row * 2^nq + col (uint64); entries in
+ *       ascending index order.  24 bytes per entry (plus a derived row
+ *       pointer of 2^nq + 1 uint64 used by the kernels).
+ *   DAS (Sec. III-A.1, Fig. 1b): per non-zero a value and a uint64 distance
+ *       word: bits 0..62 count the zeros since the previous non-zero of the
+ *       same row (or the row start), bit 63 marks the last non-zero of its
+ *       row.  Rows in order; every row needs at least one non-zero.
+ * nq <= 32 (indices need 2 nq bits).  `stream` is a cudaStream_t (NULL =
+ * legacy default); calls are asynchronous on it except *_export/*_info.
+ * Objects are owned by the caller and freed with *_destroy. */
+typedef struct mera_dax mera_dax;
+typedef struct mera_das mera_das;
+
+/* Encode a host dense matrix (interleaved complex128, row-major, 2^nq x
+ * 2^nq, nq <= 12) by scanning it row by row. */
+int mera_dax_from_dense(const double* m, int nq, void* stream, mera_dax** out);
+int mera_das_from_dense(const double* m, int nq, void* stream, mera_das** out);
+/* Upload host arrays as given (indices ascending / distance words in row
+ * order; validated on the host). */
+int mera_dax_from_host(int nq, uint64_t nnz, const uint64_t* index, const double* vals, void* stream,
+                       mera_dax** out);
+int mera_das_from_host(int nq, uint64_t nnz, const uint64_t* dist, const double* vals, void* stream,
+                       mera_das** out);
+/* MTP (Sec. III-A.2, Fig. 2): *out = a (x) b computed on the device.  DAX:
+ * index = concatenated row bits * dim + concatenated column bits, value =
+ * product; DAS: the paper's three-case distance equation.  The result has
+ * nnz(a) * nnz(b) entries in row-major order. */
+int mera_dax_kron(const mera_dax* a, const mera_dax* b, void* stream, mera_dax** out);
+int mera_das_kron(const mera_das* a, const mera_das* b, void* stream, mera_das** out);
+/* MVM (Sec. III-A.2): out = M in, out of place (in and out distinct states
+ * of n = nq qubits, same dtype); runs on out's stream after in's work. */
+int mera_dax_mvm(const mera_dax* d, mera_state* in, mera_state* out);
+int mera_das_mvm(const mera_das* d, mera_state* in, mera_state* out);
+/* Size queries (synchronous). */
+int mera_dax_info(const mera_dax* d, int* nq, uint64_t* nnz);
+int mera_das_info(const mera_das* d, int* nq, uint64_t* nnz);
+/* Copy the entries to host arrays of nnz elements (vals: 2 nnz doubles).
+ * Synchronous. */
+int mera_dax_export(const mera_dax* d, uint64_t* index, double* vals);
+int mera_das_export(const mera_das* d, uint64_t* dist, double* vals);
+int mera_dax_destroy(mera_dax* d);
+int mera_das_destroy(mera_das* d);
 
 /* ---- kernel timing ------------------------------------------------------ */
 

@@ -6,11 +6,14 @@ resolved lazily so that ``paper_2411_15332_gb300.inputs`` (the seeded
 workload generators) imports without touching the CUDA library.
 """
 
-__all__ = ["State", "gate_matrix", "launch_count", "profile_enable", "profile_read"]
+__all__ = ["State", "DAX", "DAS", "gate_matrix", "launch_count", "profile_enable", "profile_read", "plan_summary"]
 
 
 def __getattr__(name):
-    if name in ("State", "gate_matrix", "launch_count", "profile_enable", "profile_read"):
+    if name in ("State", "gate_matrix", "launch_count", "profile_enable", "profile_read", "plan_summary"):
         from . import core
         return getattr(core, name)
+    if name in ("DAX", "DAS"):
+        from . import compressed
+        return getattr(compressed, name)
     raise AttributeError(name)

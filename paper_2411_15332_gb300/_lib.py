@@ -73,12 +73,27 @@ PROTOS = {
     "mera_apply_matrix": (I, [P, DP, IP, I, IP, I]),
     "mera_apply_circuit": (I, [P, P, SZ, I]),
     "mera_hadamard_layer": (I, [P, U64]),
+    "mera_plan_summary": (I, [I, I, P, SZ, C.c_char_p, SZ, IP]),
     "mera_norm2": (I, [P, DP]),
     "mera_expect_z": (I, [P, I, DP]),
     "mera_expect_z_sum": (I, [P, DP]),
     "mera_observables": (I, [P, I, DP]),
     "mera_argmax": (I, [P, U64P, DP]),
     "mera_measure": (I, [P, DP, SZ, U64P]),
+    "mera_dax_from_dense": (I, [DP, I, P, PP]),
+    "mera_das_from_dense": (I, [DP, I, P, PP]),
+    "mera_dax_from_host": (I, [I, U64, U64P, DP, P, PP]),
+    "mera_das_from_host": (I, [I, U64, U64P, DP, P, PP]),
+    "mera_dax_kron": (I, [P, P, P, PP]),
+    "mera_das_kron": (I, [P, P, P, PP]),
+    "mera_dax_mvm": (I, [P, P, P]),
+    "mera_das_mvm": (I, [P, P, P]),
+    "mera_dax_info": (I, [P, IP, U64P]),
+    "mera_das_info": (I, [P, IP, U64P]),
+    "mera_dax_export": (I, [P, U64P, DP]),
+    "mera_das_export": (I, [P, U64P, DP]),
+    "mera_dax_destroy": (I, [P]),
+    "mera_das_destroy": (I, [P]),
     "mera_profile_enable": (I, [I]),
     "mera_profile_read": (I, [U64P, DP, DP]),
 }
@@ -124,7 +139,7 @@ def ops_to_array(ops):
         arr[j]["cmask"] = cm
         arr[j]["cvals"] = cv
         ps = list(params)
-        if name in ("U", "U3") and len(ps) == 3:
+        if isinstance(name, str) and name in ("U", "U3") and len(ps) == 3:
             ps.append(0.0)
         for t, v in enumerate(ps):
             arr[j]["params"][t] = v

@@ -170,6 +170,17 @@ def gate_matrix(name: str, params=()) -> np.ndarray:
     return (a[0::2] + 1j * a[1::2]).reshape(d, d)
 
 
+def plan_summary(n: int, ops, dtype: str = "c128") -> str:
+    """How the fused mode would run ``ops`` (host only, no GPU needed)."""
+    arr, keep = L.ops_to_array(ops)
+    buf = C.create_string_buffer(1 << 20)
+    npass = C.c_int()
+    L.check(L.lib().mera_plan_summary(int(n), L.MERA_C128 if dtype == "c128" else L.MERA_C64,
+                                      C.c_void_p(arr.ctypes.data), len(arr), buf, len(buf), C.byref(npass)))
+    del keep
+    return buf.value.decode()
+
+
 def launch_count() -> int:
     return int(L.lib().mera_launch_count())
 

@@ -1,5 +1,6 @@
 // C ABI entry points (mera.h), error reporting, launch accounting and the
 // state object's lifetime.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -388,6 +389,25 @@ int mera_apply_circuit(mera_state* s, const mera_op* ops, size_t nops, int mode)
         return MERA_OK;
     }
     return apply_fused(s, prep);
+    API_END
+}
+
+int mera_plan_summary(int n, int dtype, const mera_op* ops, size_t nops, char* out, size_t cap, int* npasses) {
+    API_BEGIN
+    MERA_RETURN_IF(n < 5 || n > MERA_MAX_QUBITS, MERA_EINVAL, "n=%d outside [5, %d] for the fused path", n,
+                   MERA_MAX_QUBITS);
+    MERA_RETURN_IF(dtype != MERA_C64 && dtype != MERA_C128, MERA_EUNSUPPORTED, "unknown dtype %d", dtype);
+    MERA_RETURN_IF(nops > 0 && ops == nullptr, MERA_EINVAL, "ops is NULL");
+    std::vector<PrepOp> prep(nops);
+    for (size_t j = 0; j < nops; ++j) MERA_TRY(prepare_op(ops[j], n, &prep[j]));
+    std::string s;
+    MERA_TRY(plan_summary(n, dtype, prep, &s, npasses));
+    if (out && cap > 0) {
+        const size_t m = std::min(cap - 1, s.size());
+        memcpy(out, s.data(), m);
+        out[m] = 0;
+    }
+    return MERA_OK;
     API_END
 }
 

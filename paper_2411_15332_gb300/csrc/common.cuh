@@ -112,5 +112,6 @@ int gate_matrix(int gate, const double* params, int* nt, cplx* out);
 int apply_prepared(mera_state* s, const PrepOp& op);
 // Fused path (fused.cu).
 int apply_fused(mera_state* s, const std::vector<PrepOp>& ops);
+int plan_summary(int n, int dtype, const std::vector<PrepOp>& ops, std::string* out, int* npasses);
 
 }  // namespace mera

@@ -15,7 +15,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <cstdio>
 #include <cstring>
+#include <string>
 #include <vector>
 
 #include "common.cuh"
@@ -49,7 +51,12 @@ static int low_bits_for(int dtype, int K) {
 struct Pass {
     uint64_t tile_mask = 0;
     std::vector<int> ops;
+    int single = -1;     // >= 0: run this op with the per-gate kernel instead
 };
+
+// Three-target non-diagonal gates are not fused: they split the circuit and
+// run as per-gate kernels.
+static bool is_barrier(const PrepOp& P) { return P.k == 3 && P.kind != KIND_DIAG; }
 
 static uint64_t op_qubits(const PrepOp& P) {
     uint64_t m = P.cmask;
@@ -61,6 +68,21 @@ static uint64_t op_targets(const PrepOp& P) {
     for (int j = 0; j < P.k; ++j) m |= 1ull << P.t[j];
     return m;
 }
+// Exact in int64 block floating point: butterflies, moves, {1, i, -1, -i}.
+static bool op_is_exact(const PrepOp& P) {
+    if (P.is_h) return true;
+    if (P.kind != KIND_MONO && P.kind != KIND_DIAG) return false;
+    for (int s = 0; s < (1 << P.k); ++s) {
+        const cplx v = P.v[s];
+        if (!(v == cplx(1, 0) || v == cplx(-1, 0) || v == cplx(0, 1) || v == cplx(0, -1))) return false;
+    }
+    return true;
+}
+
+// Passes with at least this many Hadamard levels keep only exact gates (the
+// int64 engine); other gates wait for the next pass.
+static constexpr int I64_MIN_H = 3;
+
 static int coef_need(const PrepOp& P) {
     if (P.kind == KIND_DIAG) return 1 << P.k;
     if (P.is_h) return 0;
@@ -68,11 +90,30 @@ static int coef_need(const PrepOp& P) {
     return 1 << (2 * P.k);
 }
 
+static void plan_segment(const std::vector<PrepOp>& ops, std::vector<int> remaining, int n, int K, int L,
+                         std::vector<Pass>& passes);
+
 static std::vector<Pass> plan_passes(const std::vector<PrepOp>& ops, int n, int K, int L) {
-    std::vector<int> remaining;
-    for (int i = 0; i < (int)ops.size(); ++i)
-        if (ops[i].kind != KIND_IDENTITY) remaining.push_back(i);
     std::vector<Pass> passes;
+    std::vector<int> seg;
+    for (int i = 0; i < (int)ops.size(); ++i) {
+        if (ops[i].kind == KIND_IDENTITY) continue;
+        if (is_barrier(ops[i])) {
+            plan_segment(ops, seg, n, K, L, passes);
+            seg.clear();
+            Pass b;
+            b.single = i;
+            passes.push_back(b);
+            continue;
+        }
+        seg.push_back(i);
+    }
+    plan_segment(ops, seg, n, K, L, passes);
+    return passes;
+}
+
+static void plan_segment(const std::vector<PrepOp>& ops, std::vector<int> remaining, int n, int K, int L,
+                         std::vector<Pass>& passes) {
     const uint64_t low = (L >= 64) ? ~0ull : ((1ull << L) - 1ull);
     while (!remaining.empty()) {
         Pass p;
@@ -82,11 +123,14 @@ static std::vector<Pass> plan_passes(const std::vector<PrepOp>& ops, int n, int 
         // register phases as build_pass will form them (same order, same rule)
         uint64_t ph_need = 0;
         int nph = 1;
+        int nh = 0;
+        bool inexact = false;
         std::vector<int> deferred;
         for (int idx : remaining) {
             const PrepOp& P = ops[idx];
             const uint64_t q = op_qubits(P);
             bool take = !(q & blocked);
+            if (take && !op_is_exact(P) && nh >= I64_MIN_H) take = false;
             if (take && (nops + 1 > TILE_MAX_OPS || ncoef + coef_need(P) > TILE_MAX_COEF)) take = false;
             if (take && P.kind != KIND_DIAG) {
                 const uint64_t t = op_targets(P);
@@ -108,17 +152,19 @@ static std::vector<Pass> plan_passes(const std::vector<PrepOp>& ops, int n, int 
                 p.ops.push_back(idx);
                 ++nops;
                 ncoef += coef_need(P);
+                if (P.is_h) ++nh;
+                if (!op_is_exact(P)) inexact = true;
             } else {
                 deferred.push_back(idx);
                 blocked |= q;
             }
         }
+        (void)inexact;
         // fill the remaining tile bits with the lowest free positions
         for (int b = 0; b < n && popc(p.tile_mask) < K; ++b) p.tile_mask |= 1ull << b;
         passes.push_back(std::move(p));
         remaining.swap(deferred);
     }
-    return passes;
 }
 
 template <typename V>
@@ -129,6 +175,46 @@ static V to_v(cplx c) {
     return r;
 }
 
+// Coefficient slot of the pass: float2 for complex64 (FP engine); for
+// complex128 the int64 engine reads Q62 fixed point (value * 2^62, |value|
+// < 2) from the same 16 bytes.
+template <typename V>
+static V enc(cplx c, bool q62);
+template <>
+float2 enc<float2>(cplx c, bool) {
+    return to_v<float2>(c);
+}
+template <>
+double2 enc<double2>(cplx c, bool q62) {
+    if (!q62) return to_v<double2>(c);
+    const double s = 4611686018427387904.0;   // 2^62
+    long long q[2] = {std::llround(c.real() * s), std::llround(c.imag() * s)};
+    double2 r;
+    memcpy(&r, q, sizeof(r));
+    return r;
+}
+
+// Max absolute row sum of a 2^k x 2^k matrix (bounds the growth of one
+// application in the max norm) and whether it is unitary.
+static void op_gain(const PrepOp& P, double* rowsum, bool* unitary) {
+    const int d = 1 << P.k;
+    double best = 0.0;
+    for (int r = 0; r < d; ++r) {
+        double s = 0.0;
+        for (int c = 0; c < d; ++c) s += std::abs(P.m[r * d + c]);
+        best = std::max(best, s);
+    }
+    bool u = true;
+    for (int r = 0; r < d && u; ++r)
+        for (int c = 0; c < d && u; ++c) {
+            cplx acc = 0;
+            for (int j = 0; j < d; ++j) acc += std::conj(P.m[j * d + r]) * P.m[j * d + c];
+            if (std::abs(acc - (r == c ? cplx(1, 0) : cplx(0, 0))) > 1e-9) u = false;
+        }
+    *rowsum = best;
+    *unitary = u;
+}
+
 static int phase_code_f(cplx v) {
     if (v == cplx(1, 0)) return 0;
     if (v == cplx(0, 1)) return 1;
@@ -137,33 +223,319 @@ static int phase_code_f(cplx v) {
     return 4;
 }
 
-// Build the kernel arguments of one pass; returns false if the pass had to
-// be cut (too many phases) -- the caller then re-plans with smaller passes.
+static uint32_t unit_exp(cplx v) { return (uint32_t)phase_code_f(v); }
+
+// Host-side builder of one pass: kernel arguments plus the separable
+// diagonal tables (appended to `tabs`, offsets relative to its start).
 template <typename V>
-static int build_pass(const std::vector<PrepOp>& ops, const Pass& p, int K, PassArgs<V>& A, int n) {
-    memset(&A, 0, sizeof(A));
-    A.K = K;
+struct PassBuilder {
+    PassArgs<V>& A;
+    std::vector<V>& tabs;
+    const std::vector<PrepOp>& ops;
+    int K, n;
     int local_of[64];
-    for (int q = 0; q < 64; ++q) local_of[q] = -1;
-    int j = 0;
-    for (int q = 0; q < n; ++q)
-        if ((p.tile_mask >> q) & 1ull) {
-            A.tpos[j] = q;
-            local_of[q] = j++;
+    int nop = 0, ncoef = 0, nz4 = 0, nnt = 0;
+    bool i64 = false;
+
+    PassBuilder(PassArgs<V>& a, std::vector<V>& t, const std::vector<PrepOp>& o, int k, int nn)
+        : A(a), tabs(t), ops(o), K(k), n(nn) {}
+
+    int add_op(TileOp** out) {
+        MERA_RETURN_IF(nop >= TILE_MAX_OPS, MERA_EUNSUPPORTED, "tile pass op table full");
+        *out = &A.ops[nop++];
+        **out = TileOp();
+        (*out)->coef = ncoef;
+        return MERA_OK;
+    }
+    int add_coef(cplx c) {
+        MERA_RETURN_IF(ncoef >= TILE_MAX_COEF, MERA_EUNSUPPORTED, "tile pass coefficient table full");
+        A.coef[ncoef++] = enc<V>(c, i64);
+        return MERA_OK;
+    }
+
+    // A run of diagonal gates (they commute): single-qubit factors become one
+    // separable diagonal (or exact Z4 terms when all are unit phases), unit-
+    // phase multi-qubit patterns become Z4 terms, the rest stay as they are.
+    int flush_diag(const std::vector<int>& run) {
+        if (run.empty()) return MERA_OK;
+        cplx lam[64][2];
+        bool has[64] = {false};
+        std::vector<Z4Term> terms;
+        std::vector<int> others;
+        for (int idx : run) {
+            const PrepOp& P = ops[idx];
+            int q = -1;
+            cplx v0, v1;
+            if (P.k == 1 && P.cmask == 0) {
+                q = P.t[0];
+                v0 = P.v[0];
+                v1 = P.v[1];
+            } else if (P.k == 0 && popc(P.cmask) == 1) {
+                q = __builtin_ctzll(P.cmask);
+                if (P.cvals) { v0 = 1; v1 = P.v[0]; }
+                else { v0 = P.v[0]; v1 = 1; }
+            }
+            if (q >= 0) {
+                if (!has[q]) { lam[q][0] = 1; lam[q][1] = 1; has[q] = true; }
+                lam[q][0] *= v0;
+                lam[q][1] *= v1;
+                continue;
+            }
+            if (P.k == 0 && phase_code_f(P.v[0]) <= 3) {
+                Z4Term z{};
+                z.mask = P.cmask;
+                z.vals = P.cvals;
+                z.e = (int)unit_exp(P.v[0]);
+                terms.push_back(z);
+                continue;
+            }
+            others.push_back(idx);
         }
-    // phases
-    struct Ph {
-        uint32_t need = 0;
-        int begin = 0, end = 0;
-    };
-    std::vector<Ph> phs;
-    Ph cur;
-    cur.begin = 0;
-    int nh = 0;
-    for (int i = 0; i < (int)p.ops.size(); ++i) {
-        const PrepOp& P = ops[p.ops[i]];
-        if (P.is_h) ++nh;
-        if (P.kind != KIND_DIAG) {
+        bool general = false;
+        for (int q = 0; q < n; ++q)
+            if (has[q] && (phase_code_f(lam[q][0]) > 3 || phase_code_f(lam[q][1]) > 3)) general = true;
+        if (!general) {
+            for (int q = 0; q < n; ++q) {
+                if (!has[q]) continue;
+                for (int b = 0; b < 2; ++b) {
+                    const uint32_t e = unit_exp(lam[q][b]);
+                    if (e == 0) continue;
+                    Z4Term z{};
+                    z.mask = 1ull << q;
+                    z.vals = b ? (1ull << q) : 0ull;
+                    z.e = (int)e;
+                    terms.push_back(z);
+                }
+            }
+        }
+        if (!terms.empty()) {
+            MERA_RETURN_IF(nz4 + (int)terms.size() > TILE_MAX_Z4, MERA_EUNSUPPORTED, "too many sign terms");
+            TileOp* o;
+            MERA_TRY(add_op(&o));
+            o->type = TOP_Z4;
+            o->aux = nz4;
+            o->aux2 = (int)terms.size();
+            for (const Z4Term& z : terms) A.z4[nz4++] = z;
+        }
+        if (general) {
+            // table over the tile-local qubits (times lam[0] of every other
+            // qubit); the first DSEP_SEL_BITS non-tile qubits select one of
+            // 2^m tables pre-multiplied by lam[1]/lam[0] where their bit is 1,
+            // further non-tile factors are applied per tile
+            TileOp* o;
+            MERA_TRY(add_op(&o));
+            o->type = TOP_DSEP;
+            o->aux = (int)tabs.size();
+            o->aux2 = nnt;
+            cplx base = 1;
+            std::vector<cplx> rho;
+            for (int q = 0; q < n; ++q) {
+                if (!has[q] || local_of[q] >= 0) continue;
+                base *= lam[q][0];
+                MERA_RETURN_IF(nnt >= TILE_MAX_NT, MERA_EUNSUPPORTED, "too many non-tile diagonal factors");
+                A.ntq[nnt++] = (int8_t)q;
+                rho.push_back(lam[q][1] / lam[q][0]);
+            }
+            const int nf = (int)rho.size();
+            const int nsel = std::min(nf, DSEP_SEL_BITS);
+            for (int f = nsel; f < nf; ++f) MERA_TRY(add_coef(rho[f]));
+            o->nt = (int8_t)nf;
+            const size_t T = (size_t)1 << K;
+            const size_t off = tabs.size();
+            tabs.resize(off + (T << nsel));
+            for (size_t sel = 0; sel < ((size_t)1 << nsel); ++sel) {
+                cplx b = base;
+                for (int f = 0; f < nsel; ++f)
+                    if ((sel >> f) & 1) b *= rho[f];
+                for (size_t l = 0; l < T; ++l) {
+                    cplx d = b;
+                    for (int j = 0; j < K; ++j) {
+                        const int q = A.tpos[j];
+                        if (has[q]) d *= lam[q][(l >> j) & 1];
+                    }
+                    tabs[off + (sel << K) + l] = enc<V>(d, i64);
+                }
+            }
+        }
+        for (int idx : others) {
+            const PrepOp& P = ops[idx];
+            TileOp* o;
+            MERA_TRY(add_op(&o));
+            o->type = TOP_DIAG;
+            o->cmask = P.cmask;
+            o->cvals = P.cvals;
+            o->nt = (int8_t)P.k;
+            for (int t = 0; t < P.k; ++t) o->tq[t] = (int8_t)P.t[t];
+            for (int s2 = 0; s2 < (1 << P.k); ++s2) {
+                MERA_TRY(add_coef(P.v[s2]));
+                if (P.v[s2] != cplx(1, 0)) o->flags |= 1u << s2;
+                o->codes |= (uint32_t)phase_code_f(P.v[s2]) << (3 * s2);
+            }
+        }
+        return MERA_OK;
+    }
+
+    int add_gate(const PrepOp& P, const int* reg_of) {
+        TileOp* o;
+        MERA_TRY(add_op(&o));
+        o->cmask = P.cmask;
+        o->cvals = P.cvals;
+        int rr[3];
+        for (int t = 0; t < P.k; ++t) rr[t] = reg_of[local_of[P.t[t]]];
+        if (P.k == 1) {
+            o->a = (int8_t)rr[0];
+            if (P.is_h) {
+                o->type = TOP_H;
+            } else if (P.kind == KIND_MONO) {
+                o->type = TOP_G1MONO;
+                for (int s2 = 0; s2 < 2; ++s2) {
+                    MERA_TRY(add_coef(P.v[s2]));
+                    o->codes |= (uint32_t)phase_code_f(P.v[s2]) << (3 * s2);
+                }
+            } else {
+                o->type = TOP_G1;
+                for (int s2 = 0; s2 < 4; ++s2) MERA_TRY(add_coef(P.m[s2]));
+            }
+            return MERA_OK;
+        }
+        // k = 2: register bits in descending order; conv maps the register
+        // sub-index to the gate's sub-index
+        const int k = P.k;
+        int order[3] = {0, 1, 2};
+        std::sort(order, order + k, [&](int x, int y) { return rr[x] > rr[y]; });
+        o->a = (int8_t)rr[order[0]];
+        o->b = (int8_t)rr[order[1]];
+        auto conv = [&](int sr) {
+            int sg = 0;
+            for (int pos = 0; pos < k; ++pos) {
+                const int bit = (sr >> (k - 1 - pos)) & 1;   // register slot pos (0 = most significant)
+                sg |= bit << (k - 1 - order[pos]);
+            }
+            return sg;
+        };
+        int inv[8];
+        for (int sr = 0; sr < (1 << k); ++sr) inv[conv(sr)] = sr;
+        const int d = 1 << k;
+        if (P.kind == KIND_MONO) {
+            o->type = TOP_G2MONO;
+            for (int sr = 0; sr < d; ++sr) {
+                const int sg = conv(sr);
+                MERA_TRY(add_coef(P.v[sg]));
+                o->codes |= (uint32_t)phase_code_f(P.v[sg]) << (3 * sr);
+                o->perm |= (uint32_t)inv[P.perm[sg]] << (3 * sr);
+            }
+        } else {
+            o->type = TOP_G2;
+            for (int sr = 0; sr < d; ++sr)
+                for (int cr = 0; cr < d; ++cr) MERA_TRY(add_coef(P.m[conv(sr) * d + conv(cr)]));
+        }
+        return MERA_OK;
+    }
+
+    // op kinds present in the built pass
+    int features() const {
+        int f = 0;
+        for (int i = 0; i < nop; ++i) {
+            switch (A.ops[i].type) {
+            case TOP_G1: f |= FEAT_DENSE1; break;
+            case TOP_G2:
+            case TOP_G2MONO: f |= FEAT_G2; break;
+            case TOP_DIAG:
+            case TOP_DSEP: f |= FEAT_DIAG; break;
+            default: break;
+            }
+        }
+        return f;
+    }
+
+    int build(const Pass& p, bool allow_i64) {
+        memset(&A, 0, sizeof(A));
+        A.K = K;
+        for (int q = 0; q < 64; ++q) local_of[q] = -1;
+        int j = 0;
+        for (int q = 0; q < n; ++q)
+            if ((p.tile_mask >> q) & 1ull) {
+                A.tpos[j] = q;
+                local_of[q] = j++;
+            }
+        // engine: complex128 passes with at least I64_MIN_H Hadamard levels run
+        // the int64 engine (exact integer butterflies); the others stay in
+        // float64, where moves and sign flips are exact and a folded diagonal
+        // run costs one complex multiply per amplitude
+        int nh = 0;
+        bool all_unitary = true;
+        double gain_bits = 0.0;
+        for (int idx : p.ops) {
+            const PrepOp& P = ops[idx];
+            if (P.is_h) {
+                ++nh;
+                continue;
+            }
+            double rs;
+            bool u;
+            op_gain(P, &rs, &u);
+            all_unitary = all_unitary && u;
+            if (rs > 1.0) gain_bits += std::log2(rs);
+        }
+        A.nh = nh;
+        bool exact = true;
+        for (int idx : p.ops) exact = exact && op_is_exact(ops[idx]);
+        i64 = allow_i64 && exact && nh >= I64_MIN_H;
+        A.scale = std::pow(0.5, nh / 2) * ((nh & 1) ? (1.0 / std::sqrt(2.0)) : 1.0);
+        // fixed-point headroom: the max-norm bound (every op's row sum), or
+        // for unitary passes the tile 2-norm bound 2^((nh + K) / 2)
+        double g = nh + gain_bits;
+        if (all_unitary) g = std::min(g, std::ceil((nh + K) / 2.0));
+        A.guard = (int)std::ceil(g) + 1;
+        if (A.guard > 28) i64 = false;   // too little fixed-point precision left: float64
+        // Merge diagonal runs: a diagonal gate moves past the non-diagonal
+        // gates it commutes with (no shared target: a diagonal commutes with
+        // gates that only use its qubits as controls), but only when that
+        // brings it next to another diagonal run, first looking forward,
+        // then backward.  Non-commuting pairs keep their order.
+        std::vector<int> order(p.ops.begin(), p.ops.end());
+        auto is_diag = [&](int pos) { return ops[order[pos]].kind == KIND_DIAG; };
+        for (int i = (int)order.size() - 1; i >= 0; --i) {
+            if (!is_diag(i)) continue;
+            const uint64_t dq = op_qubits(ops[order[i]]);
+            if (i + 1 < (int)order.size() && !is_diag(i + 1)) {
+                int j = i + 1;
+                while (j < (int)order.size() && !is_diag(j) && !(op_targets(ops[order[j]]) & dq)) ++j;
+                if (j < (int)order.size() && is_diag(j)) {
+                    const int d = order[i];
+                    order.erase(order.begin() + i);
+                    order.insert(order.begin() + (j - 1), d);
+                    continue;
+                }
+            }
+        }
+        for (int i = 0; i < (int)order.size(); ++i) {
+            if (!is_diag(i) || i == 0 || is_diag(i - 1)) continue;
+            const uint64_t dq = op_qubits(ops[order[i]]);
+            int j = i - 1;
+            while (j >= 0 && !is_diag(j) && !(op_targets(ops[order[j]]) & dq)) --j;
+            if (j >= 0 && is_diag(j)) {
+                const int d = order[i];
+                order.erase(order.begin() + i);
+                order.insert(order.begin() + (j + 1), d);
+            }
+        }
+        Pass q = p;
+        q.ops = order;
+        return build_phases(q);
+    }
+
+    int build_phases(const Pass& p) {
+        // phases (same rule as plan_passes)
+        struct Ph {
+            uint32_t need = 0;
+            int begin = 0, end = 0;
+        };
+        std::vector<Ph> phs;
+        Ph cur;
+        for (int i = 0; i < (int)p.ops.size(); ++i) {
+            const PrepOp& P = ops[p.ops[i]];
+            if (P.kind == KIND_DIAG) continue;
             uint32_t need = 0;
             for (int t = 0; t < P.k; ++t) need |= 1u << local_of[P.t[t]];
             if (popc(cur.need | need) > FR) {
@@ -176,108 +548,111 @@ static int build_pass(const std::vector<PrepOp>& ops, const Pass& p, int K, Pass
                 cur.need |= need;
             }
         }
-    }
-    cur.end = (int)p.ops.size();
-    phs.push_back(cur);
-    MERA_RETURN_IF((int)phs.size() > TILE_MAX_PHASES, MERA_EUNSUPPORTED, "tile pass with %zu phases", phs.size());
-    A.nph = (int)phs.size();
-    A.scale = std::pow(0.5, nh / 2) * ((nh & 1) ? (1.0 / std::sqrt(2.0)) : 1.0);
-    int ncoef = 0, nop = 0;
-    for (int ph = 0; ph < A.nph; ++ph) {
-        uint32_t rbm = phs[ph].need;
-        for (int b = K - 1; b >= 0 && popc(rbm) < FR; --b)
-            if (!((rbm >> b) & 1u)) rbm |= 1u << b;
-        int reg_of[16];
-        int r = 0;
-        for (int b = 0; b < K; ++b) {
-            reg_of[b] = -1;
-            if ((rbm >> b) & 1u) {
-                A.ph[ph].rb[r] = (int8_t)b;
-                reg_of[b] = r++;
+        cur.end = (int)p.ops.size();
+        phs.push_back(cur);
+        MERA_RETURN_IF((int)phs.size() > TILE_MAX_PHASES, MERA_EUNSUPPORTED, "tile pass with %zu phases", phs.size());
+        A.nph = (int)phs.size();
+        for (int ph = 0; ph < A.nph; ++ph) {
+            uint32_t rbm = phs[ph].need;
+            for (int b = K - 1; b >= 0 && popc(rbm) < FR; --b)
+                if (!((rbm >> b) & 1u)) rbm |= 1u << b;
+            int reg_of[16];
+            int r = 0;
+            for (int b = 0; b < K; ++b) {
+                reg_of[b] = -1;
+                if ((rbm >> b) & 1u) {
+                    A.ph[ph].rb[r] = (int8_t)b;
+                    reg_of[b] = r++;
+                }
             }
+            A.ph[ph].op_begin = (int16_t)nop;
+            std::vector<int> run;
+            for (int i = phs[ph].begin; i < phs[ph].end; ++i) {
+                const PrepOp& P = ops[p.ops[i]];
+                if (P.kind == KIND_DIAG) {
+                    run.push_back(p.ops[i]);
+                    continue;
+                }
+                MERA_TRY(flush_diag(run));
+                run.clear();
+                MERA_TRY(add_gate(P, reg_of));
+            }
+            MERA_TRY(flush_diag(run));
+            A.ph[ph].op_end = (int16_t)nop;
         }
-        A.ph[ph].op_begin = (int16_t)nop;
-        for (int i = phs[ph].begin; i < phs[ph].end; ++i) {
-            const PrepOp& P = ops[p.ops[i]];
-            TileOp& o = A.ops[nop++];
-            o.cmask = P.cmask;
-            o.cvals = P.cvals;
-            o.coef = ncoef;
-            if (P.kind == KIND_DIAG) {
-                o.type = TOP_DIAG;
-                o.nt = (int8_t)P.k;
-                for (int t = 0; t < P.k; ++t) o.tq[t] = (int8_t)P.t[t];
-                for (int s = 0; s < (1 << P.k); ++s) {
-                    A.coef[ncoef++] = to_v<V>(P.v[s]);
-                    if (P.v[s] != cplx(1, 0)) o.flags |= 1u << s;
-                    o.codes |= (uint32_t)phase_code_f(P.v[s]) << (3 * s);
-                }
-                continue;
-            }
-            int rr[3];
-            for (int t = 0; t < P.k; ++t) rr[t] = reg_of[local_of[P.t[t]]];
-            if (P.k == 1) {
-                o.a = (int8_t)rr[0];
-                if (P.is_h) {
-                    o.type = TOP_H;
-                } else if (P.kind == KIND_MONO) {
-                    o.type = TOP_G1MONO;
-                    for (int s = 0; s < 2; ++s) {
-                        A.coef[ncoef++] = to_v<V>(P.v[s]);
-                        o.codes |= (uint32_t)phase_code_f(P.v[s]) << (3 * s);
-                    }
-                } else {
-                    o.type = TOP_G1;
-                    for (int s = 0; s < 4; ++s) A.coef[ncoef++] = to_v<V>(P.m[s]);
-                }
-                continue;
-            }
-            // k = 2, 3: order the register bits descending; conv maps the
-            // register sub-index to the gate's sub-index
-            const int k = P.k;
-            int order[3] = {0, 1, 2};
-            std::sort(order, order + k, [&](int x, int y) { return rr[x] > rr[y]; });
-            o.a = (int8_t)rr[order[0]];
-            o.b = (int8_t)rr[order[1]];
-            if (k == 3) o.c = (int8_t)rr[order[2]];
-            auto conv = [&](int sr) {
-                int sg = 0;
-                for (int pos = 0; pos < k; ++pos) {
-                    const int bit = (sr >> (k - 1 - pos)) & 1;   // register slot pos (0 = most significant)
-                    const int t = order[pos];                     // gate target in that slot
-                    sg |= bit << (k - 1 - t);
-                }
-                return sg;
-            };
-            int inv[8];
-            for (int sr = 0; sr < (1 << k); ++sr) inv[conv(sr)] = sr;
-            const int d = 1 << k;
-            if (P.kind == KIND_MONO) {
-                o.type = k == 2 ? TOP_G2MONO : TOP_G3MONO;
-                for (int sr = 0; sr < d; ++sr) {
-                    const int sg = conv(sr);
-                    A.coef[ncoef++] = to_v<V>(P.v[sg]);
-                    o.codes |= (uint32_t)phase_code_f(P.v[sg]) << (3 * sr);
-                    o.perm |= (uint32_t)inv[P.perm[sg]] << (3 * sr);
-                }
-            } else {
-                o.type = k == 2 ? TOP_G2 : TOP_G3;
-                for (int sr = 0; sr < d; ++sr)
-                    for (int cr = 0; cr < d; ++cr) A.coef[ncoef++] = to_v<V>(P.m[conv(sr) * d + conv(cr)]);
-            }
-        }
-        A.ph[ph].op_end = (int16_t)nop;
+        // stage the first load / last store through shared memory unless the
+        // lanes cover whole 128-byte rows in global memory
+        const int S = sizeof(V) == 16 ? 3 : 4;
+        auto low_reg = [&](int ph) {
+            for (int r = 0; r < FR; ++r)
+                if (A.ph[ph].rb[r] < S) return true;
+            return false;
+        };
+        A.load_smem = low_reg(0) ? 1 : 0;
+        A.store_smem = low_reg(A.nph - 1) ? 1 : 0;
+        return MERA_OK;
     }
-    // stage the first load / last store through shared memory unless the
-    // lanes cover whole 128-byte rows in global memory
-    const int S = sizeof(V) == 16 ? 3 : 4;
-    auto low_reg = [&](int ph) {
-        for (int r = 0; r < FR; ++r)
-            if (A.ph[ph].rb[r] < S) return true;
-        return false;
-    };
-    A.load_smem = low_reg(0) ? 1 : 0;
-    A.store_smem = low_reg(A.nph - 1) ? 1 : 0;
+};
+
+// Kernel variants: complex128 has the int64 engine and feature-trimmed
+// instantiations (register pressure); complex64 has one full FP variant.
+using TileFn = void (*)(PassArgs<double2>);
+template <typename V>
+struct TileVariant {
+    const void* fn;
+    int eng, feat;
+};
+
+static const void* tile_fn_c128(int eng, int feat) {
+    if (eng == ENG_I64) {
+        switch (feat) {
+        case 0: return (const void*)k_tile<double2, ENG_I64, 0>;
+        case FEAT_DIAG: return (const void*)k_tile<double2, ENG_I64, FEAT_DIAG>;
+        default: return (const void*)k_tile<double2, ENG_I64, FEAT_ALL>;
+        }
+    }
+    switch (feat) {
+    case 0: return (const void*)k_tile<double2, ENG_FP, 0>;
+    case FEAT_DIAG: return (const void*)k_tile<double2, ENG_FP, FEAT_DIAG>;
+    default: return (const void*)k_tile<double2, ENG_FP, FEAT_ALL>;
+    }
+}
+
+// Smallest compiled variant that covers the requested features.
+static int round_feat(int, int feat, bool c128) {
+    if (!c128) return FEAT_ALL;
+    if (feat == 0) return 0;
+    if (feat == FEAT_DIAG) return FEAT_DIAG;
+    return FEAT_ALL;
+}
+
+template <typename V>
+static int launch_tile(int eng, int feat, unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+                       const PassArgs<V>& A);
+template <>
+int launch_tile<double2>(int eng, int feat, unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+                         const PassArgs<double2>& A) {
+    const void* fn = tile_fn_c128(eng, feat);
+    // opt in to the tile's dynamic shared memory (once per variant and size)
+    static std::vector<std::pair<const void*, size_t>> opted;
+    if (smem > 48 * 1024 && std::find(opted.begin(), opted.end(), std::make_pair(fn, smem)) == opted.end()) {
+        MERA_CHECK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        opted.push_back(std::make_pair(fn, smem));
+    }
+    void* args[] = {const_cast<PassArgs<double2>*>(&A)};
+    MERA_CHECK_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, st));
+    return MERA_OK;
+}
+template <>
+int launch_tile<float2>(int, int, unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+                        const PassArgs<float2>& A) {
+    static size_t opted = 0;
+    if (smem > 48 * 1024 && smem > opted) {
+        MERA_CHECK_CUDA(cudaFuncSetAttribute(k_tile<float2, ENG_FP, FEAT_ALL>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        opted = smem;
+    }
+    k_tile<float2, ENG_FP, FEAT_ALL><<<grid, block, smem, st>>>(A);
     return MERA_OK;
 }
 
@@ -287,29 +662,98 @@ static int run_fused(mera_state* s, const std::vector<PrepOp>& ops) {
     const int K = fused_tile_bits(s->dtype, n);
     const int L = low_bits_for(s->dtype, K);
     std::vector<Pass> passes = plan_passes(ops, n, K, L);
+    if (passes.empty()) return MERA_OK;
     // opt in to the dynamic shared memory of a full tile (2^K elements)
     const size_t tile_bytes = ((size_t)1 << K) * sizeof(V);
     MERA_RETURN_IF(tile_bytes > 227 * 1024, MERA_EUNSUPPORTED, "tile of %zu bytes exceeds shared memory", tile_bytes);
-    static int attr_set[2] = {0, 0};
-    const int slot = sizeof(V) == 16 ? 1 : 0;
-    if (attr_set[slot] < (int)tile_bytes) {
-        MERA_CHECK_CUDA(cudaFuncSetAttribute(k_tile<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_bytes));
-        attr_set[slot] = (int)tile_bytes;
+    const bool allow_i64 = sizeof(V) == 16;
+    // build every pass first: the diagonal tables go up in one copy
+    std::vector<PassArgs<V>> args(passes.size());
+    std::vector<unsigned char> eng(passes.size()), feat(passes.size());
+    std::vector<V> tabs;
+    for (size_t i = 0; i < passes.size(); ++i) {
+        if (passes[i].single >= 0) continue;
+        PassBuilder<V> b(args[i], tabs, ops, K, n);
+        MERA_TRY(b.build(passes[i], allow_i64));
+        eng[i] = b.i64 ? 1 : 0;
+        feat[i] = (unsigned char)round_feat(eng[i], b.features(), sizeof(V) == 16);
     }
-    std::vector<unsigned char> buf(sizeof(PassArgs<V>));
-    PassArgs<V>& A = *reinterpret_cast<PassArgs<V>*>(buf.data());
-    for (const Pass& p : passes) {
-        MERA_TRY(build_pass<V>(ops, p, K, A, n));
+    const V* dtab = nullptr;
+    if (!tabs.empty()) {
+        const size_t bytes = tabs.size() * sizeof(V);
+        if (s->prog_bytes < bytes) {
+            MERA_CHECK_CUDA(cudaStreamSynchronize(s->stream));   // earlier passes may read the old tables
+            if (s->prog) cudaFree(s->prog);
+            s->prog = nullptr;
+            s->prog_bytes = 0;
+            cudaError_t e = cudaMalloc(&s->prog, bytes);
+            if (e != cudaSuccess) {
+                set_error("cudaMalloc(%zu) for diagonal tables: %s", bytes, cudaGetErrorString(e));
+                return MERA_ENOMEM;
+            }
+            s->prog_bytes = bytes;
+        }
+        // pageable source: the call returns once the host buffer was consumed
+        MERA_CHECK_CUDA(cudaMemcpyAsync(s->prog, tabs.data(), bytes, cudaMemcpyHostToDevice, s->stream));
+        dtab = reinterpret_cast<const V*>(s->prog);
+    }
+    const uint64_t tiles = 1ull << (n - K);
+    MERA_RETURN_IF(tiles > 0x7fffffffull, MERA_EUNSUPPORTED, "too many tiles");
+    for (size_t i = 0; i < passes.size(); ++i) {
+        if (passes[i].single >= 0) {
+            MERA_TRY(apply_prepared(s, ops[passes[i].single]));
+            continue;
+        }
+        PassArgs<V>& A = args[i];
         A.psi = reinterpret_cast<V*>(s->data);
+        A.tab = dtab;
         const bool need_sm = A.nph > 1 || A.load_smem || A.store_smem;
-        const size_t smem = need_sm ? ((size_t)1 << K) * sizeof(V) : 0;
-        const uint64_t tiles = 1ull << (n - K);
-        MERA_RETURN_IF(tiles > 0x7fffffffull, MERA_EUNSUPPORTED, "too many tiles");
+        const size_t smem = need_sm ? tile_bytes : 0;
         launch_begin(s->stream, MERA_KCLASS_TILE, 2.0 * (double)num_amps(s) * sizeof(V));
-        k_tile<V><<<(unsigned)tiles, 1u << (K - FR), smem, s->stream>>>(A);
+        MERA_TRY(launch_tile<V>(eng[i], feat[i], (unsigned)tiles, 1u << (K - FR), smem, s->stream, A));
         MERA_TRY(launch_end(s->stream));
     }
     return MERA_OK;
+}
+
+// Host-only description of the plan (no device work).
+template <typename V>
+static int describe_fused(int n, int dtype, const std::vector<PrepOp>& ops, std::string* out, int* npasses) {
+    const int K = fused_tile_bits(dtype, n);
+    const int L = low_bits_for(dtype, K);
+    std::vector<Pass> passes = plan_passes(ops, n, K, L);
+    std::vector<V> tabs;
+    std::vector<unsigned char> buf(sizeof(PassArgs<V>));
+    PassArgs<V>& A = *reinterpret_cast<PassArgs<V>*>(buf.data());
+    char line[512];
+    snprintf(line, sizeof(line), "K=%d L=%d passes=%zu\n", K, L, passes.size());
+    *out += line;
+    for (size_t i = 0; i < passes.size(); ++i) {
+        if (passes[i].single >= 0) {
+            snprintf(line, sizeof(line), "pass %zu: per-gate op %d\n", i, passes[i].single);
+            *out += line;
+            continue;
+        }
+        PassBuilder<V> b(A, tabs, ops, K, n);
+        MERA_TRY(b.build(passes[i], sizeof(V) == 16));
+        int cnt[10] = {0};
+        for (int o = 0; o < b.nop; ++o) cnt[A.ops[o].type]++;
+        std::string bits;
+        for (int j = 0; j < K; ++j) bits += std::to_string(A.tpos[j]) + (j + 1 < K ? "," : "");
+        snprintf(line, sizeof(line),
+                 "pass %zu: eng=%s nh=%d phases=%d ops=%d [g1=%d mono=%d h=%d g2=%d diag=%d dsep=%d z4=%d] "
+                 "guard=%d load_smem=%d store_smem=%d tile={%s}\n",
+                 i, b.i64 ? "i64" : "fp", A.nh, A.nph, b.nop, cnt[TOP_G1], cnt[TOP_G1MONO] + cnt[TOP_G2MONO], cnt[TOP_H],
+                 cnt[TOP_G2], cnt[TOP_DIAG], cnt[TOP_DSEP], cnt[TOP_Z4], A.guard, A.load_smem, A.store_smem, bits.c_str());
+        *out += line;
+    }
+    if (npasses) *npasses = (int)passes.size();
+    return MERA_OK;
+}
+
+int plan_summary(int n, int dtype, const std::vector<PrepOp>& ops, std::string* out, int* npasses) {
+    if (dtype == MERA_C128) return describe_fused<double2>(n, dtype, ops, out, npasses);
+    return describe_fused<float2>(n, dtype, ops, out, npasses);
 }
 
 int apply_fused(mera_state* s, const std::vector<PrepOp>& ops) {

@@ -40,18 +40,56 @@ __device__ __forceinline__ V cdot2(V m0, V x0, V m1, V x1) {
     return cfma(m1, x1, acc);
 }
 
+// int64 fixed-point complex (block floating point inside a fused tile).
+// Coefficients are Q62: value * 2^62 as int64 (|value| < 2).
+struct __align__(16) I2 {
+    long long x, y;
+};
+
+// (a * c) >> 62 with the full 128-bit product (truncating).
+__device__ __forceinline__ long long mulq62(long long a, long long c) {
+    const long long hi = __mul64hi(a, c);
+    const unsigned long long lo = (unsigned long long)a * (unsigned long long)c;
+    return (long long)(((unsigned long long)hi << 2) | (lo >> 62));
+}
+// c * a for a Q62 coefficient c
+__device__ __forceinline__ I2 cmul(I2 c, I2 a) {
+    I2 r;
+    r.x = mulq62(c.x, a.x) - mulq62(c.y, a.y);
+    r.y = mulq62(c.x, a.y) + mulq62(c.y, a.x);
+    return r;
+}
+__device__ __forceinline__ I2 cfma(I2 c, I2 a, I2 acc) {
+    acc.x += mulq62(c.x, a.x) - mulq62(c.y, a.y);
+    acc.y += mulq62(c.x, a.y) + mulq62(c.y, a.x);
+    return acc;
+}
+__device__ __forceinline__ long long sneg(long long v) { return -v; }
+__device__ __forceinline__ I2 neg_v(I2 x) {
+    x.x = -x.x;
+    x.y = -x.y;
+    return x;
+}
+
 // Multiply by a phase given as a code: 0 -> 1, 1 -> i, 2 -> -1, 3 -> -i
 // (exact: only moves and sign flips), 4 -> the general value v.
-__device__ __forceinline__ double2 neg_v(double2 x) { return make_double2(-x.x, -x.y); }
-__device__ __forceinline__ float2 neg_v(float2 x) { return make_float2(-x.x, -x.y); }
+// Sign flips as integer operations on the sign bit (no FP64 instruction).
+__device__ __forceinline__ double dneg(double v) {
+    return __hiloint2double(__double2hiint(v) ^ (int)0x80000000, __double2loint(v));
+}
+__device__ __forceinline__ float fneg(float v) { return __int_as_float(__float_as_int(v) ^ (int)0x80000000); }
+__device__ __forceinline__ double sneg(double v) { return dneg(v); }
+__device__ __forceinline__ float sneg(float v) { return fneg(v); }
+__device__ __forceinline__ double2 neg_v(double2 x) { return make_double2(dneg(x.x), dneg(x.y)); }
+__device__ __forceinline__ float2 neg_v(float2 x) { return make_float2(fneg(x.x), fneg(x.y)); }
 template <typename V>
 __device__ __forceinline__ V apply_phase(int code, V v, V x) {
     V r;
     switch (code) {
     case 0: return x;
-    case 1: r.x = -x.y; r.y = x.x; return r;
+    case 1: r = x; r.x = sneg(x.y); r.y = x.x; return r;
     case 2: return neg_v(x);
-    case 3: r.x = x.y; r.y = -x.x; return r;
+    case 3: r = x; r.x = x.y; r.y = sneg(x.x); return r;
     default: return cmul(v, x);
     }
 }

@@ -11,7 +11,23 @@
 // through shared memory.  High qubits enter the tile by being named in
 // tpos: the tile is gathered from HBM with those qubits as local bits,
 // which is the qubit-index swap done on the fly.
+//
+// Arithmetic engines.  GB300 issues about two FP64 FMAs per clock per SM
+// against ~114 FP32 FMAs and ~80 integer adds, so complex128 work avoids
+// FP64 where it can:
+//  * ENG_FP  : float32 arithmetic for complex64 states.
+//  * ENG_I64 : complex128 states.  The tile is converted once to int64
+//              block floating point (one exponent per tile): butterflies are
+//              exact integer adds, permutations and {1, i, -1, -i} phases are
+//              moves and sign flips, and every multiplication is a Q62
+//              fixed-point product (full 128-bit product, ~13 integer ops);
+//              the pass's 2^{-m/2} Hadamard scale is applied on the way out.
+// In both engines a run of diagonal gates folds into exact sign / i terms
+// (TOP_Z4) and one table lookup plus one complex multiply per amplitude
+// (TOP_DSEP).
 #pragma once
+
+#include <type_traits>
 
 #include "kernels.cuh"
 
@@ -20,8 +36,16 @@ namespace mera {
 constexpr int FR = 4;              // register bits per thread
 constexpr int FRA = 1 << FR;       // amplitudes per thread
 constexpr int TILE_MAX_PHASES = 32;
-constexpr int TILE_MAX_OPS = 192;
+constexpr int TILE_MAX_OPS = 160;
 constexpr int TILE_MAX_COEF = 448;
+constexpr int TILE_MAX_Z4 = 96;
+constexpr int TILE_MAX_NT = 48;    // non-tile factors of separable diagonals
+
+enum TileEngine { ENG_FP = 0, ENG_I64 = 1 };
+
+// Kernel variants by the op kinds a pass holds (H, monomial 1-target and Z4
+// are always compiled in): fewer op bodies, fewer live registers.
+enum TileFeature { FEAT_DIAG = 1, FEAT_DENSE1 = 2, FEAT_G2 = 4, FEAT_ALL = 7 };
 
 enum TileOpType : int8_t {
     TOP_G1 = 0,       // dense 2x2 on one register bit (coef[0..3])
@@ -29,22 +53,31 @@ enum TileOpType : int8_t {
     TOP_H = 2,        // unscaled Hadamard butterfly (pass scale at the end)
     TOP_G2 = 3,       // dense 4x4 on register bits a > b
     TOP_G2MONO = 4,   // monomial 4x4: row s takes phase(s) * amp perm(s)
-    TOP_G3 = 5,       // dense 8x8 on register bits a > b > c
-    TOP_G3MONO = 6,
+    // 5, 6: unused (three-target gates run as per-gate kernels between passes)
     TOP_DIAG = 7,     // diagonal on any bits: amp *= v[sub] where flagged
+    TOP_DSEP = 8,     // separable diagonal: amp *= tab[local index] * prod(non-tile factors)
+    TOP_Z4 = 9,       // product of exact phases i^e over pattern terms
 };
 
 struct TileOp {
     int8_t type;
-    int8_t a, b, c;      // register bits (a is the most significant sub-index bit)
-    int8_t nt;           // diag: number of targets
+    int8_t a, b, c;      // register bits (a is the most significant sub-index bit; c unused)
+    int8_t nt;           // diag: number of targets; dsep: non-tile factors
     int8_t tq[3];        // diag: global target positions (tq[0] most significant)
     int32_t coef;        // first coefficient in PassArgs::coef
     uint32_t flags;      // diag: bit s set when sub-index s changes
     uint32_t codes;      // phase codes, 3 bits per row / sub-index
     uint32_t perm;       // monomial: source sub-index of row s, 3 bits per row
+    int32_t aux;         // dsep: table offset (elements); z4: first term
+    int32_t aux2;        // dsep: first non-tile position; z4: number of terms
     uint64_t cmask;      // control qubits (global positions)
     uint64_t cvals;      // their required values
+};
+
+struct Z4Term {
+    uint64_t mask, vals;  // amplitude gets i^e when (index & mask) == vals
+    int32_t e;
+    int32_t pad;
 };
 
 struct TilePhase {
@@ -55,24 +88,38 @@ struct TilePhase {
 template <typename V>
 struct PassArgs {
     V* psi;
+    const V* tab;        // separable-diagonal tables (device), 2^K entries each
     int K;               // tile bits
     int nph;             // phases
     int load_smem;       // 1: stage the first phase's load through shared memory
     int store_smem;      // 1: stage the last phase's store through shared memory
-    double scale;        // applied to every amplitude at the end of the pass
+    double scale;        // ENG_FP: applied at the end of the pass
+    int nh;              // Hadamard butterflies in the pass (ENG_I64 scales by 2^-nh/2)
+    int guard;           // ENG_I64: headroom bits of the fixed-point format
     int tpos[16];        // global bit of local bit j, ascending
+    int8_t ntq[TILE_MAX_NT];   // global positions of separable non-tile factors
     TilePhase ph[TILE_MAX_PHASES];
     TileOp ops[TILE_MAX_OPS];
+    Z4Term z4[TILE_MAX_Z4];
     V coef[TILE_MAX_COEF];
+};
+
+template <typename V>
+struct IsFP {
+    static constexpr bool value = true;
+};
+template <>
+struct IsFP<I2> {
+    static constexpr bool value = false;
 };
 
 // ----------------------------------------------------------- bit helpers --
 // Shared-memory slot of local index l: XOR-fold the higher bit groups into
 // the lowest S bits (S = log2 of amplitudes per 128-byte row) so that the
 // strided register gathers hit distinct banks.
-template <typename V>
+template <int EB>
 __device__ __forceinline__ int swz(int l) {
-    constexpr int S = sizeof(V) == 16 ? 3 : 4;
+    constexpr int S = EB == 16 ? 3 : 4;
     constexpr int M = (1 << S) - 1;
     const int h = l >> S;
     return l ^ ((h ^ (h >> S) ^ (h >> (2 * S)) ^ (h >> (3 * S)) ^ (h >> (4 * S))) & M);
@@ -110,7 +157,46 @@ __device__ __forceinline__ T dep4(int j, const T* m) {
 
 __device__ __forceinline__ int code_at(uint32_t codes, int s) { return (int)((codes >> (3 * s)) & 7u); }
 
-// ------------------------------------------------------------ op bodies --
+// XOR of the masks of the set bits of j (slot offsets under the linear
+// swizzle).
+__device__ __forceinline__ int dep4x(int j, const int* m) {
+    int r = 0;
+    if (j & 1) r ^= m[0];
+    if (j & 2) r ^= m[1];
+    if (j & 4) r ^= m[2];
+    if (j & 8) r ^= m[3];
+    return r;
+}
+
+// 16-bit mask of this thread's register slots whose controls hold: the
+// non-register control bits are fixed for the thread, the register ones
+// select slots.
+__device__ __forceinline__ uint32_t active16(uint64_t cmask, uint64_t cvals, uint64_t gb, const uint64_t* gm) {
+    if (cmask == 0) return 0xFFFFu;
+    const uint64_t regm = gm[0] | gm[1] | gm[2] | gm[3];
+    if ((gb & cmask & ~regm) != (cvals & ~regm)) return 0u;
+    uint32_t pat = 0xFFFFu;
+    const uint32_t b1[4] = {0xAAAAu, 0xCCCCu, 0xF0F0u, 0xFF00u};
+#pragma unroll
+    for (int r = 0; r < FR; ++r)
+        if (cmask & gm[r]) pat &= (cvals & gm[r]) ? b1[r] : ~b1[r];
+    return pat & 0xFFFFu;
+}
+
+// x * i^k, branch free (k in 0..3).
+template <typename V>
+__device__ __forceinline__ V mul_ik(V x, int k) {
+    V r = x;
+    if (k & 1) {
+        r.x = x.y;
+        r.y = x.x;
+    }
+    if (k == 1 || k == 2) r.x = sneg(r.x);
+    if (k >= 2) r.y = sneg(r.y);
+    return r;
+}
+
+// --------------------------------------------------- engine primitives --
 template <typename V>
 __device__ __forceinline__ V vadd(V a, V b) {
     a.x += b.x;
@@ -123,37 +209,56 @@ __device__ __forceinline__ V vsub(V a, V b) {
     a.y -= b.y;
     return a;
 }
+
+// Exact phase codes 0..3 (moves and sign flips); code 4 multiplies by v
+// (FP, or Q62 fixed point in the int64 engine).
 template <typename V>
-__device__ __forceinline__ V vscale(V a, double s) {
-    a.x = (decltype(a.x))(a.x * s);
-    a.y = (decltype(a.y))(a.y * s);
-    return a;
+__device__ __forceinline__ V phase_any(int code, V v, V x) {
+    return apply_phase(code, v, x);
 }
 
+// Read-only table entry.
+__device__ __forceinline__ double2 tab_ld(const double2* p) { return __ldg(p); }
+__device__ __forceinline__ float2 tab_ld(const float2* p) { return __ldg(p); }
+__device__ __forceinline__ I2 tab_ld(const I2* p) {
+    const longlong2 v = __ldg(reinterpret_cast<const longlong2*>(p));
+    I2 r;
+    r.x = v.x;
+    r.y = v.y;
+    return r;
+}
+
+// ------------------------------------------------------------ op bodies --
 template <typename V, int B>
 __device__ __forceinline__ void op_g1(V (&x)[FRA], const TileOp& o, const V* cf, uint64_t gb, const uint64_t* gm) {
+    const uint32_t act = active16(o.cmask, o.cvals, gb, gm);
+    if (act == 0) return;
+    const V m0 = cf[0], m1 = cf[1], m2 = cf[2], m3 = cf[3];
 #pragma unroll
     for (int j = 0; j < FRA; ++j) {
         if (j & (1 << B)) continue;
         const int j1 = j | (1 << B);
-        if (((gb | dep4(j, gm)) & o.cmask) != o.cvals) continue;
+        if (!(act & (1u << j))) continue;
         const V a0 = x[j], a1 = x[j1];
-        x[j] = cdot2(cf[0], a0, cf[1], a1);
-        x[j1] = cdot2(cf[2], a0, cf[3], a1);
+        x[j] = cdot2(m0, a0, m1, a1);
+        x[j1] = cdot2(m2, a0, m3, a1);
     }
 }
 
 template <typename V, int B>
 __device__ __forceinline__ void op_g1mono(V (&x)[FRA], const TileOp& o, const V* cf, uint64_t gb, const uint64_t* gm) {
+    const uint32_t act = active16(o.cmask, o.cvals, gb, gm);
+    if (act == 0) return;
     const int c0 = code_at(o.codes, 0), c1 = code_at(o.codes, 1);
+    const V v0 = cf[0], v1 = cf[1];
 #pragma unroll
     for (int j = 0; j < FRA; ++j) {
         if (j & (1 << B)) continue;
         const int j1 = j | (1 << B);
-        if (((gb | dep4(j, gm)) & o.cmask) != o.cvals) continue;
+        if (!(act & (1u << j))) continue;
         const V a0 = x[j], a1 = x[j1];
-        x[j] = apply_phase(c0, cf[0], a1);
-        x[j1] = apply_phase(c1, cf[1], a0);
+        x[j] = phase_any(c0, v0, a1);
+        x[j1] = phase_any(c1, v1, a0);
     }
 }
 
@@ -172,10 +277,12 @@ __device__ __forceinline__ void op_h(V (&x)[FRA]) {
 template <typename V, int A, int B>
 __device__ __forceinline__ void op_g2(V (&x)[FRA], const TileOp& o, const V* cf, uint64_t gb, const uint64_t* gm,
                                       bool mono) {
+    const uint32_t act = active16(o.cmask, o.cvals, gb, gm);
+    if (act == 0) return;
 #pragma unroll
     for (int j = 0; j < FRA; ++j) {
         if (j & ((1 << A) | (1 << B))) continue;
-        if (((gb | dep4(j, gm)) & o.cmask) != o.cvals) continue;
+        if (!(act & (1u << j))) continue;
         const int id[4] = {j, j | (1 << B), j | (1 << A), j | (1 << A) | (1 << B)};
         V in[4];
 #pragma unroll
@@ -188,7 +295,7 @@ __device__ __forceinline__ void op_g2(V (&x)[FRA], const TileOp& o, const V* cf,
 #pragma unroll
                 for (int u = 1; u < 4; ++u)
                     if (src == u) v = in[u];
-                x[id[s]] = apply_phase(code_at(o.codes, s), cf[s], v);
+                x[id[s]] = phase_any(code_at(o.codes, s), cf[s], v);
             }
         } else {
 #pragma unroll
@@ -202,60 +309,76 @@ __device__ __forceinline__ void op_g2(V (&x)[FRA], const TileOp& o, const V* cf,
     }
 }
 
-template <typename V, int A, int B, int C>
-__device__ __forceinline__ void op_g3(V (&x)[FRA], const TileOp& o, const V* cf, uint64_t gb, const uint64_t* gm,
-                                      bool mono) {
-#pragma unroll
-    for (int j = 0; j < FRA; ++j) {
-        if (j & ((1 << A) | (1 << B) | (1 << C))) continue;
-        if (((gb | dep4(j, gm)) & o.cmask) != o.cvals) continue;
-        int id[8];
-#pragma unroll
-        for (int s = 0; s < 8; ++s)
-            id[s] = j | ((s & 4) ? (1 << A) : 0) | ((s & 2) ? (1 << B) : 0) | ((s & 1) ? (1 << C) : 0);
-        V in[8];
-#pragma unroll
-        for (int s = 0; s < 8; ++s) in[s] = x[id[s]];
-        if (mono) {
-#pragma unroll
-            for (int s = 0; s < 8; ++s) {
-                const int src = (int)((o.perm >> (3 * s)) & 7u);
-                V v = in[0];
-#pragma unroll
-                for (int u = 1; u < 8; ++u)
-                    if (src == u) v = in[u];
-                x[id[s]] = apply_phase(code_at(o.codes, s), cf[s], v);
-            }
-        } else {
-#pragma unroll
-            for (int r = 0; r < 8; ++r) {
-                V acc = cmul(cf[r * 8], in[0]);
-#pragma unroll
-                for (int c = 1; c < 8; ++c) acc = cfma(cf[r * 8 + c], in[c], acc);
-                x[id[r]] = acc;
-            }
-        }
-    }
-}
-
 template <typename V>
 __device__ __forceinline__ void op_diag(V (&x)[FRA], const TileOp& o, const V* cf, uint64_t gb, const uint64_t* gm) {
+    const uint32_t act = active16(o.cmask, o.cvals, gb, gm);
+    if (act == 0) return;
 #pragma unroll
     for (int j = 0; j < FRA; ++j) {
+        if (!(act & (1u << j))) continue;
         const uint64_t g = gb | dep4(j, gm);
-        if ((g & o.cmask) != o.cvals) continue;
         int sub = 0;
         for (int t = 0; t < o.nt; ++t) sub = (sub << 1) | (int)((g >> o.tq[t]) & 1ull);
-        if ((o.flags >> sub) & 1u) x[j] = apply_phase(code_at(o.codes, sub), cf[sub], x[j]);
+        if ((o.flags >> sub) & 1u) x[j] = phase_any(code_at(o.codes, sub), cf[sub], x[j]);
     }
 }
 
+// Exact phase i^(sum of matching terms' exponents).  The 16 exponents are
+// kept mod 4 as two 16-bit planes; each term adds its exponent to the
+// slots its pattern selects.
 template <typename V>
-__device__ __forceinline__ void apply_tile_op(V (&x)[FRA], const TileOp& o, const V* cf, uint64_t gb,
-                                              const uint64_t* gm) {
+__device__ __forceinline__ void op_z4(V (&x)[FRA], const TileOp& o, const Z4Term* z4, uint64_t gb, const uint64_t* gm) {
+    uint32_t p0 = 0, p1 = 0;
+    for (int t = 0; t < o.aux2; ++t) {
+        const Z4Term z = z4[o.aux + t];
+        const uint32_t act = active16(z.mask, z.vals, gb, gm);
+        if (z.e & 1) {
+            const uint32_t c = p0 & act;
+            p0 ^= act;
+            p1 ^= c;
+        }
+        if (z.e & 2) p1 ^= act;
+    }
+    if ((p0 | p1) == 0) return;
+#pragma unroll
+    for (int j = 0; j < FRA; ++j) x[j] = mul_ik(x[j], (int)(((p0 >> j) & 1u) | (((p1 >> j) & 1u) << 1)));
+}
+
+// Separable diagonal: the product over tile-local qubits comes from a table
+// indexed by the local index.  Up to DSEP_SEL_BITS non-tile qubits select
+// one of 2^m pre-multiplied tables (the tile's bits are fixed); beyond that
+// the remaining non-tile factors multiply in per tile.
+constexpr int DSEP_SEL_BITS = 3;
+
+template <typename V>
+__device__ __forceinline__ void op_dsep(V (&x)[FRA], const TileOp& o, const V* cf, const V* tab, const int8_t* ntq,
+                                        uint32_t lb, const int* lm, uint64_t gb, int K) {
+    const int nsel = o.nt < DSEP_SEL_BITS ? o.nt : DSEP_SEL_BITS;
+    uint32_t sel = 0;
+    for (int f = 0; f < nsel; ++f) sel |= (uint32_t)((gb >> ntq[o.aux2 + f]) & 1ull) << f;
+    const V* t = tab + o.aux + ((size_t)sel << K);
+    bool have_c = false;
+    V c = cf[0];
+    for (int f = nsel; f < o.nt; ++f) {
+        if ((gb >> ntq[o.aux2 + f]) & 1ull) {
+            c = have_c ? cmul(c, cf[f - nsel]) : cf[f - nsel];
+            have_c = true;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < FRA; ++j) {
+        V d = tab_ld(t + (lb | dep4(j, lm)));
+        if (have_c) d = cmul(c, d);
+        x[j] = cmul(d, x[j]);
+    }
+}
+
+template <typename V, typename SV, int FEAT>
+__device__ __forceinline__ void apply_tile_op(V (&x)[FRA], const TileOp& o, const PassArgs<SV>& a, const V* cf,
+                                              uint64_t gb, const uint64_t* gm, uint32_t lb, const int* lm) {
     switch (o.type) {
     case TOP_G1:
-        switch (o.a) {
+        if constexpr ((FEAT & FEAT_DENSE1) != 0) switch (o.a) {
         case 0: op_g1<V, 0>(x, o, cf, gb, gm); break;
         case 1: op_g1<V, 1>(x, o, cf, gb, gm); break;
         case 2: op_g1<V, 2>(x, o, cf, gb, gm); break;
@@ -281,8 +404,8 @@ __device__ __forceinline__ void apply_tile_op(V (&x)[FRA], const TileOp& o, cons
     case TOP_G2:
     case TOP_G2MONO: {
         const bool mono = o.type == TOP_G2MONO;
-        switch (o.a * 4 + o.b) {
-        case 1: op_g2<V, 1, 0>(x, o, cf, gb, gm, mono); break;
+        if constexpr ((FEAT & FEAT_G2) != 0) switch (o.a * 4 + o.b) {
+        case 1 * 4 + 0: op_g2<V, 1, 0>(x, o, cf, gb, gm, mono); break;
         case 2 * 4 + 0: op_g2<V, 2, 0>(x, o, cf, gb, gm, mono); break;
         case 2 * 4 + 1: op_g2<V, 2, 1>(x, o, cf, gb, gm, mono); break;
         case 3 * 4 + 0: op_g2<V, 3, 0>(x, o, cf, gb, gm, mono); break;
@@ -291,32 +414,94 @@ __device__ __forceinline__ void apply_tile_op(V (&x)[FRA], const TileOp& o, cons
         }
         break;
     }
-    case TOP_G3:
-    case TOP_G3MONO: {
-        const bool mono = o.type == TOP_G3MONO;
-        switch (6 - o.a - o.b - o.c) {   // a > b > c in 0..3: the missing bit names the triple
-        case 3: op_g3<V, 2, 1, 0>(x, o, cf, gb, gm, mono); break;
-        case 2: op_g3<V, 3, 1, 0>(x, o, cf, gb, gm, mono); break;
-        case 1: op_g3<V, 3, 2, 0>(x, o, cf, gb, gm, mono); break;
-        default: op_g3<V, 3, 2, 1>(x, o, cf, gb, gm, mono); break;
-        }
+    case TOP_DIAG:
+        if constexpr ((FEAT & FEAT_DIAG) != 0) op_diag<V>(x, o, cf, gb, gm);
         break;
-    }
-    default: op_diag<V>(x, o, cf, gb, gm); break;
+    case TOP_Z4: op_z4<V>(x, o, a.z4, gb, gm); break;
+    default:
+        if constexpr ((FEAT & FEAT_DIAG) != 0)
+            op_dsep<V>(x, o, cf, reinterpret_cast<const V*>(a.tab), a.ntq, lb, lm, gb, a.K);
+        break;
     }
 }
 
+// ------------------------------------------- int64 block floating point --
+// Biased exponent field of a double (0 for zero / subnormal).
+__device__ __forceinline__ int dexp(double v) {
+    return (int)((__double_as_longlong(v) >> 52) & 0x7FF);
+}
+
+// round(v * 2^S) as int64, for |v| * 2^S < 2^62 (subnormals read as 0).
+__device__ __forceinline__ long long d2fix(double v, int S) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)((b >> 52) & 0x7FF);
+    if (e == 0) return 0;
+    const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = S + e - 1075;
+    unsigned long long a;
+    if (sh >= 0) a = m << sh;
+    else if (sh > -64) a = (m + (1ull << (-sh - 1))) >> (-sh);
+    else a = 0;
+    return (b >> 63) ? -(long long)a : (long long)a;
+}
+
+// v * 2^-S rounded to nearest even (values below the normal range flush to 0).
+__device__ __forceinline__ double fix2d(long long v, int S) {
+    if (v == 0) return 0.0;
+    const unsigned long long sgn = v < 0 ? (1ull << 63) : 0ull;
+    const unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+    int lz = __clzll((long long)a);
+    const unsigned long long m = a << lz;
+    unsigned long long r = m >> 11;
+    const unsigned long long rem = m & 0x7FFull;
+    if (rem > 0x400ull || (rem == 0x400ull && (r & 1ull))) {
+        r += 1;
+        if (r >> 53) {
+            r >>= 1;
+            lz -= 1;
+        }
+    }
+    const int e = (63 - lz) - S + 1023;
+    if (e <= 0) return __longlong_as_double((long long)sgn);
+    return __longlong_as_double((long long)(sgn | ((unsigned long long)e << 52) | (r & 0xFFFFFFFFFFFFFull)));
+}
+
 // ---------------------------------------------------------------- kernel --
-template <typename V>
-__global__ void __launch_bounds__(512) k_tile(const __grid_constant__ PassArgs<V> a) {
+// Raw bits of a stored value, held in the int64 engine's registers until the
+// tile exponent is known.
+template <typename SV, typename V>
+__device__ __forceinline__ V raw_load(const SV v) {
+    if constexpr (IsFP<V>::value) {
+        return v;
+    } else {
+        V r;
+        r.x = __double_as_longlong(v.x);
+        r.y = __double_as_longlong(v.y);
+        return r;
+    }
+}
+
+// SV: storage type (double2 / float2); ENG selects the arithmetic, FEAT the
+// op kinds compiled in.
+// complex128: two CTAs per SM for the lightest variant, one (with up to 255
+// registers, no spills) when multiplying op bodies are compiled in.
+template <typename SV, int ENG, int FEAT>
+__global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
+                                  (sizeof(SV) == 16 && (FEAT == 0 || (ENG == ENG_FP && FEAT == FEAT_DIAG))) ? 2 : 1)
+    k_tile(const __grid_constant__ PassArgs<SV> a) {
+    using V = typename std::conditional<ENG == ENG_I64, I2, SV>::type;
+    constexpr int EB = sizeof(SV);
     extern __shared__ __align__(16) unsigned char smraw[];
-    V* sm = reinterpret_cast<V*>(smraw);
+    SV* sms = reinterpret_cast<SV*>(smraw);     // staging of stored values
+    V* sm = reinterpret_cast<V*>(smraw);        // exchange between phases
+    __shared__ int s_emax[16];
     const int K = a.K;
     const uint32_t T = 1u << (K - FR);
     const uint32_t tid = threadIdx.x;
     const uint64_t tile = blockIdx.x;
     const uint64_t tb = insert_zeros(tile, a.tpos, K);    // global index of local 0
     V x[FRA];
+    int S = 0;   // ENG_I64: fixed-point exponent
 
     if (a.load_smem) {
         // coalesced copy: element tid + i*T, its top FR local bits come from i
@@ -324,10 +509,12 @@ __global__ void __launch_bounds__(512) k_tile(const __grid_constant__ PassArgs<V
         uint64_t gtop[FR];
 #pragma unroll
         for (int r = 0; r < FR; ++r) gtop[r] = 1ull << a.tpos[K - FR + r];
+        int st[FR];
 #pragma unroll
-        for (int i = 0; i < FRA; ++i) x[i] = a.psi[gt | dep4(i, gtop)];
+        for (int r = 0; r < FR; ++r) st[r] = swz<EB>((int)(T << r));
+        const int s0 = swz<EB>((int)tid);
 #pragma unroll
-        for (int i = 0; i < FRA; ++i) sm[swz<V>((int)(tid + i * T))] = x[i];
+        for (int i = 0; i < FRA; ++i) sms[s0 ^ dep4x(i, st)] = a.psi[gt | dep4(i, gtop)];
         __syncthreads();
     }
 
@@ -336,46 +523,102 @@ __global__ void __launch_bounds__(512) k_tile(const __grid_constant__ PassArgs<V
         const uint32_t lb = insert_reg_zeros(tid, ph.rb);
         const uint64_t gb = tb | spread_bits(lb, a.tpos, K);
         uint64_t gm[FR];
-        int lm[FR];
+        int lm[FR], sr[FR];
 #pragma unroll
         for (int r = 0; r < FR; ++r) {
             gm[r] = 1ull << a.tpos[ph.rb[r]];
             lm[r] = 1 << ph.rb[r];
+            sr[r] = swz<EB>(lm[r]);
         }
-        if (p == 0 && !a.load_smem) {
+        const int sb = swz<EB>((int)lb);   // swizzle is XOR-linear: slot = sb ^ xor of sr
+        if (p == 0) {
+            if (!a.load_smem) {
 #pragma unroll
-            for (int j = 0; j < FRA; ++j) x[j] = a.psi[gb | dep4(j, gm)];
+                for (int j = 0; j < FRA; ++j) x[j] = raw_load<SV, V>(a.psi[gb | dep4(j, gm)]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < FRA; ++j) x[j] = raw_load<SV, V>(sms[sb ^ dep4x(j, sr)]);
+            }
+            if constexpr (ENG == ENG_I64) {
+                // tile exponent: max over the tile of both components
+                int e = 0;
+#pragma unroll
+                for (int j = 0; j < FRA; ++j)
+                    e = max(e, max((int)((x[j].x >> 52) & 0x7FF), (int)((x[j].y >> 52) & 0x7FF)));
+                const unsigned amask = T >= 32 ? 0xffffffffu : ((1u << T) - 1u);
+                e = (int)__reduce_max_sync(amask, (unsigned)e);
+                if ((tid & 31) == 0) s_emax[tid >> 5] = e;
+                __syncthreads();
+                int emax = 0;
+                for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) emax = max(emax, s_emax[w]);
+                // |v| < 2^(emax-1022); the pass grows it by at most 2^(guard-1)
+                S = emax == 0 ? 0 : 62 - a.guard - (emax - 1022);
+#pragma unroll
+                for (int j = 0; j < FRA; ++j) {
+                    x[j].x = d2fix(__longlong_as_double(x[j].x), S);
+                    x[j].y = d2fix(__longlong_as_double(x[j].y), S);
+                }
+            }
         } else {
 #pragma unroll
-            for (int j = 0; j < FRA; ++j) x[j] = sm[swz<V>((int)(lb | dep4(j, lm)))];
+            for (int j = 0; j < FRA; ++j) x[j] = sm[sb ^ dep4x(j, sr)];
         }
         for (int o = ph.op_begin; o < ph.op_end; ++o) {
             const TileOp& op = a.ops[o];
-            apply_tile_op<V>(x, op, a.coef + op.coef, gb, gm);
+            apply_tile_op<V, SV, FEAT>(x, op, a, reinterpret_cast<const V*>(a.coef) + op.coef, gb, gm, lb, lm);
         }
-        const bool last = (p == a.nph - 1);
-        if (last && a.scale != 1.0) {
-#pragma unroll
-            for (int j = 0; j < FRA; ++j) x[j] = vscale(x[j], a.scale);
-        }
-        if (last && !a.store_smem) {
-#pragma unroll
-            for (int j = 0; j < FRA; ++j) a.psi[gb | dep4(j, gm)] = x[j];
-        } else {
+        if (p != a.nph - 1) {
             // each slot is read and written by its owner only within a phase
 #pragma unroll
-            for (int j = 0; j < FRA; ++j) sm[swz<V>((int)(lb | dep4(j, lm)))] = x[j];
+            for (int j = 0; j < FRA; ++j) sm[sb ^ dep4x(j, sr)] = x[j];
             __syncthreads();
+            continue;
         }
-    }
-
-    if (a.store_smem) {
-        const uint64_t gt = tb | spread_bits(tid, a.tpos, K - FR);
-        uint64_t gtop[FR];
+        // last phase: back to the storage type, then out
+        SV* out = reinterpret_cast<SV*>(x);
+        if constexpr (ENG == ENG_I64) {
+            // undo the fixed-point scale and apply 2^(-nh/2)
+            const int So = S + (a.nh >> 1);
+            const bool odd = a.nh & 1;
+            const long long r2 = 3260954456333195553ll;   // round(2^62 / sqrt(2))
 #pragma unroll
-        for (int r = 0; r < FR; ++r) gtop[r] = 1ull << a.tpos[K - FR + r];
+            for (int j = 0; j < FRA; ++j) {
+                long long vx = x[j].x, vy = x[j].y;
+                if (odd) {
+                    vx = __mul64hi(vx, r2) << 2;
+                    vy = __mul64hi(vy, r2) << 2;
+                }
+                x[j].x = __double_as_longlong(fix2d(vx, So));
+                x[j].y = __double_as_longlong(fix2d(vy, So));
+            }
+        } else {
+            if (a.scale != 1.0) {
 #pragma unroll
-        for (int i = 0; i < FRA; ++i) a.psi[gt | dep4(i, gtop)] = sm[swz<V>((int)(tid + i * T))];
+                for (int j = 0; j < FRA; ++j) {
+                    x[j].x = (decltype(x[j].x))(x[j].x * a.scale);
+                    x[j].y = (decltype(x[j].y))(x[j].y * a.scale);
+                }
+            }
+        }
+        if (!a.store_smem) {
+#pragma unroll
+            for (int j = 0; j < FRA; ++j) a.psi[gb | dep4(j, gm)] = out[j];
+        } else {
+            // a thread rewrites only the slots it read itself in this phase
+#pragma unroll
+            for (int j = 0; j < FRA; ++j) sms[sb ^ dep4x(j, sr)] = out[j];
+            __syncthreads();
+            const uint64_t gt = tb | spread_bits(tid, a.tpos, K - FR);
+            uint64_t gtop[FR];
+#pragma unroll
+            for (int r = 0; r < FR; ++r) gtop[r] = 1ull << a.tpos[K - FR + r];
+            int st[FR];
+#pragma unroll
+            for (int r = 0; r < FR; ++r) st[r] = swz<EB>((int)(T << r));
+            const int s0 = swz<EB>((int)tid);
+#pragma unroll
+            for (int i = 0; i < FRA; ++i) a.psi[gt | dep4(i, gtop)] = sms[s0 ^ dep4x(i, st)];
+        }
     }
 }
 
