@@ -198,6 +198,25 @@ int mera_argmax(mera_state* s, uint64_t* idx, double* prob);
  * host arrays of k elements. */
 int mera_measure(mera_state* s, const double* u, size_t k, uint64_t* idx_out);
 
+/* The same three sums as mera_observables, for callers that cannot let a
+ * library allocate device memory: code whose framework's caching allocator
+ * owns all device memory, or latency-critical loops that cannot afford the
+ * device synchronisation cudaMalloc / cudaFree may cause.  The paper has no
+ * counterpart; this is an interface convenience.
+ *   dev_psi : device pointer to 2^n amplitudes of `dtype` (16-byte aligned),
+ *             not modified; stream : cudaStream_t to run on (NULL = legacy
+ *             default); out : host array of 3 doubles (norm^2, <Z_q>,
+ *             sum_q <Z_q>).  Synchronous.
+ * Nothing is allocated: the partial sums live in one fixed device array of
+ * 3 * 1024 + 8 doubles (24.6 KB) that every GPU loading the library holds
+ * until the process exits; n is limited to 1..MERA_MAX_QUBITS (larger n is
+ * rejected with MERA_EINVAL).  The first call on a device looks up the
+ * array's device address (make that first call before any stream capture).
+ * All calls share the array and it keeps the last call's contents (each
+ * call overwrites every partial it reads, so nothing needs clearing); calls
+ * that overlap on the GPU, e.g. on two streams at once, race on it. */
+int mera_observables_noalloc(const void* dev_psi, int n, int dtype, int q, void* stream, double out[3]);
+
 /* ---- DAX / DAS compressed operation matrices (Sec. III-A) ---------------
  *
  * Device-resident, materialised forms of a 2^nq x 2^nq operation matrix:

@@ -78,6 +78,7 @@ PROTOS = {
     "mera_expect_z": (I, [P, I, DP]),
     "mera_expect_z_sum": (I, [P, DP]),
     "mera_observables": (I, [P, I, DP]),
+    "mera_observables_noalloc": (I, [P, I, I, I, P, DP]),
     "mera_argmax": (I, [P, U64P, DP]),
     "mera_measure": (I, [P, DP, SZ, U64P]),
     "mera_dax_from_dense": (I, [DP, I, P, PP]),
