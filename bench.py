@@ -124,6 +124,23 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------- helpers -------
+def max_over_ranks(value: float, device=None) -> float:
+    """Largest value over the ranks of the default process group (the
+    slowest replica's time); the value itself without a group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, slowest_ms: float) -> float:
+    """Whole-job rate: every replica's units over the slowest replica's time."""
+    return units_per_rank * world / (slowest_ms / 1e3)
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -261,13 +278,9 @@ def run_mera(args, rank, world, local_rank):
     prof = mera.profile_read()
     mera.profile_enable(False)
     clocks = clock.stop()
-    total_ms = ev[0].elapsed_time(ev[-1])
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(ev[0].elapsed_time(ev[-1]), device="cuda")
     ms_per_step = total_ms / args.steps
-    value = upd * world / (ms_per_step / 1e3)
+    value = job_throughput(upd, world, ms_per_step)
 
     # roofline of the dominant kernel (the fused tile pass)
     peak, peak_kind = _peaks()

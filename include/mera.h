@@ -264,6 +264,44 @@ int mera_das_export(const mera_das* d, uint64_t* dist, double* vals);
 int mera_dax_destroy(mera_dax* d);
 int mera_das_destroy(mera_das* d);
 
+/* ---- batched QNN ansatz and adjoint gradients ----------------------------
+ *
+ * The hardware-efficient ansatz stands in for the paper's QNN neuron
+ * (Sec. IV-D, Table III; its circuit figure is not reproducible): L layers,
+ * each RY(theta[l][0][q]) then RZ(theta[l][1][q]) on every qubit q, then the
+ * ring CNOT(q -> q+1 mod n) for q = 0..n-1.  A batch owns `capacity` states
+ * ("slots") of n qubits (5 <= n <= 26), plus as many adjoint work states.
+ * Rows of one call are independent: a slot's result does not depend on the
+ * other slots of the call.  Angles are host arrays of float64; calls are
+ * asynchronous on the batch's stream except *_observables and the
+ * gradient.  Objects are freed with mera_batch_destroy. */
+typedef struct mera_batch mera_batch;
+
+int mera_batch_create(int n, int capacity, int dtype, void* stream, mera_batch** out);
+int mera_batch_destroy(mera_batch* b);
+/* Device pointer of the 2 * capacity states (slot s at s * 2^n; the
+ * adjoint state of slot s at (capacity + s) * 2^n). */
+int mera_batch_info(const mera_batch* b, void** dev_states, int* n, int* capacity, int* dtype);
+int mera_batch_set_stream(mera_batch* b, void* stream);
+/* Copy the state of slot `slot` (0 <= slot < 2 * capacity; adjoint states
+ * from capacity on) to host memory of 2^n amplitudes.  Synchronous. */
+int mera_batch_copy_to_host(mera_batch* b, int slot, void* host);
+/* Set the listed slots (slots[nslots], NULL = 0..nslots-1) to |0...0>. */
+int mera_batch_reset(mera_batch* b, const int* slots, int nslots);
+/* One ansatz layer on each listed slot with its own angles:
+ * theta[nslots][2][n] (row j: RY angles then RZ angles of slot slots[j]). */
+int mera_batch_layer(mera_batch* b, const int* slots, int nslots, const double* theta);
+/* Slots 0..nslots-1: reset, then L layers; theta[nslots][L][2][n]. */
+int mera_batch_forward(mera_batch* b, int nslots, int L, const double* theta);
+/* out[nslots][3] = (norm^2, <Z_q>, sum_q <Z_q>) per listed slot, float64
+ * accumulation in the fixed order of mera_observables.  Synchronous. */
+int mera_batch_observables(mera_batch* b, const int* slots, int nslots, int q, double* out);
+/* Adjoint differentiation (reverse sweep with inverse gates) of
+ * loss_b = sum_q <Z_q> of the ansatz on slots 0..nslots-1:
+ * loss[nslots], grad[nslots][L][2][n] = d loss_b / d theta[b][l][g][q].
+ * Runs the forward pass itself.  Synchronous. */
+int mera_adjoint_grad(mera_batch* b, int nslots, int L, const double* theta, double* loss, double* grad);
+
 /* ---- kernel timing ------------------------------------------------------ */
 
 /* Kernel classes timed when profiling is on. */

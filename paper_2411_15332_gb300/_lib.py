@@ -95,6 +95,16 @@ PROTOS = {
     "mera_das_export": (I, [P, U64P, DP]),
     "mera_dax_destroy": (I, [P]),
     "mera_das_destroy": (I, [P]),
+    "mera_batch_create": (I, [I, I, I, P, PP]),
+    "mera_batch_destroy": (I, [P]),
+    "mera_batch_info": (I, [P, PP, IP, IP, IP]),
+    "mera_batch_set_stream": (I, [P, P]),
+    "mera_batch_copy_to_host": (I, [P, I, P]),
+    "mera_batch_reset": (I, [P, IP, I]),
+    "mera_batch_layer": (I, [P, IP, I, DP]),
+    "mera_batch_forward": (I, [P, I, I, DP]),
+    "mera_batch_observables": (I, [P, IP, I, I, DP]),
+    "mera_adjoint_grad": (I, [P, I, I, DP, DP, DP]),
     "mera_profile_enable": (I, [I]),
     "mera_profile_read": (I, [U64P, DP, DP]),
 }

@@ -101,6 +101,8 @@ struct PrepOp {
     int nact = 0;              // rows that change something
     int act[8] = {0};
     bool is_h = false;         // plain Hadamard (the RH / butterfly path)
+    int bslot = -1;            // >= 0: 2x2 matrix differs per state of a batch,
+                               //       coefficients at bslot * 4 of the state's table
 };
 
 // Validates and builds a PrepOp.  Returns MERA_OK or an error code.

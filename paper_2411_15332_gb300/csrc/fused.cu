@@ -21,7 +21,7 @@
 #include <vector>
 
 #include "common.cuh"
-#include "tile.cuh"
+#include "fused.cuh"
 
 namespace mera {
 
@@ -84,6 +84,7 @@ static bool op_is_exact(const PrepOp& P) {
 static constexpr int I64_MIN_H = 3;
 
 static int coef_need(const PrepOp& P) {
+    if (P.bslot >= 0) return 0;
     if (P.kind == KIND_DIAG) return 1 << P.k;
     if (P.is_h) return 0;
     if (P.kind == KIND_MONO) return 1 << P.k;
@@ -197,6 +198,11 @@ double2 enc<double2>(cplx c, bool q62) {
 // Max absolute row sum of a 2^k x 2^k matrix (bounds the growth of one
 // application in the max norm) and whether it is unitary.
 static void op_gain(const PrepOp& P, double* rowsum, bool* unitary) {
+    if (P.bslot >= 0) {   // per-state unitary 2x2
+        *rowsum = std::sqrt(2.0);
+        *unitary = true;
+        return;
+    }
     const int d = 1 << P.k;
     double best = 0.0;
     for (int r = 0; r < d; ++r) {
@@ -384,7 +390,11 @@ struct PassBuilder {
         for (int t = 0; t < P.k; ++t) rr[t] = reg_of[local_of[P.t[t]]];
         if (P.k == 1) {
             o->a = (int8_t)rr[0];
-            if (P.is_h) {
+            if (P.bslot >= 0) {
+                o->type = TOP_G1;
+                o->c = 1;                 // per-state coefficients
+                o->coef = P.bslot * 4;
+            } else if (P.is_h) {
                 o->type = TOP_H;
             } else if (P.kind == KIND_MONO) {
                 o->type = TOP_G1MONO;
@@ -627,10 +637,10 @@ static int round_feat(int, int feat, bool c128) {
 }
 
 template <typename V>
-static int launch_tile(int eng, int feat, unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+static int launch_tile(int eng, int feat, dim3 grid, unsigned block, size_t smem, cudaStream_t st,
                        const PassArgs<V>& A);
 template <>
-int launch_tile<double2>(int eng, int feat, unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+int launch_tile<double2>(int eng, int feat, dim3 grid, unsigned block, size_t smem, cudaStream_t st,
                          const PassArgs<double2>& A) {
     const void* fn = tile_fn_c128(eng, feat);
     // opt in to the tile's dynamic shared memory (once per variant and size)
@@ -640,11 +650,11 @@ int launch_tile<double2>(int eng, int feat, unsigned grid, unsigned block, size_
         opted.push_back(std::make_pair(fn, smem));
     }
     void* args[] = {const_cast<PassArgs<double2>*>(&A)};
-    MERA_CHECK_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, st));
+    MERA_CHECK_CUDA(cudaLaunchKernel(fn, grid, dim3(block), args, smem, st));
     return MERA_OK;
 }
 template <>
-int launch_tile<float2>(int, int, unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+int launch_tile<float2>(int, int, dim3 grid, unsigned block, size_t smem, cudaStream_t st,
                         const PassArgs<float2>& A) {
     static size_t opted = 0;
     if (smem > 48 * 1024 && smem > opted) {
@@ -656,31 +666,61 @@ int launch_tile<float2>(int, int, unsigned grid, unsigned block, size_t smem, cu
     return MERA_OK;
 }
 
+// Build every pass of a circuit: kernel arguments (without state pointers),
+// engine and kernel variant per pass, and the diagonal tables.  Passes with
+// `single` >= 0 are per-gate ops (returned in `singles`, -1 otherwise).
+template <typename V>
+int fused_build(int n, const std::vector<PrepOp>& ops, FusedPlan<V>& plan) {
+    plan.K = fused_tile_bits(sizeof(V) == 16 ? MERA_C128 : MERA_C64, n);
+    plan.n = n;
+    const int L = low_bits_for(sizeof(V) == 16 ? MERA_C128 : MERA_C64, plan.K);
+    std::vector<Pass> passes = plan_passes(ops, n, plan.K, L);
+    const size_t tile_bytes = ((size_t)1 << plan.K) * sizeof(V);
+    MERA_RETURN_IF(tile_bytes > 227 * 1024, MERA_EUNSUPPORTED, "tile of %zu bytes exceeds shared memory", tile_bytes);
+    plan.args.assign(passes.size(), PassArgs<V>());
+    plan.eng.assign(passes.size(), 0);
+    plan.feat.assign(passes.size(), 0);
+    plan.single.assign(passes.size(), -1);
+    plan.tabs.clear();
+    for (size_t i = 0; i < passes.size(); ++i) {
+        if (passes[i].single >= 0) {
+            plan.single[i] = passes[i].single;
+            continue;
+        }
+        PassBuilder<V> b(plan.args[i], plan.tabs, ops, plan.K, n);
+        MERA_TRY(b.build(passes[i], sizeof(V) == 16));
+        plan.eng[i] = b.i64 ? 1 : 0;
+        plan.feat[i] = (unsigned char)round_feat(plan.eng[i], b.features(), sizeof(V) == 16);
+    }
+    return MERA_OK;
+}
+
+// Launch pass i of a plan over `ny` states (batch rows).
+template <typename V>
+int fused_launch(const FusedPlan<V>& plan, size_t i, PassArgs<V>& A, unsigned ny, cudaStream_t st) {
+    const int K = plan.K;
+    const bool need_sm = A.nph > 1 || A.load_smem || A.store_smem;
+    const size_t smem = need_sm ? ((size_t)1 << K) * sizeof(V) : 0;
+    const uint64_t tiles = 1ull << (plan.n - K);
+    MERA_RETURN_IF(tiles > 0x7fffffffull, MERA_EUNSUPPORTED, "too many tiles");
+    MERA_RETURN_IF(ny == 0 || ny > 65535, MERA_EUNSUPPORTED, "batch of %u states per launch", ny);
+    launch_begin(st, MERA_KCLASS_TILE, 2.0 * (double)(1ull << plan.n) * sizeof(V) * ny);
+    MERA_TRY(launch_tile<V>(plan.eng[i], plan.feat[i], dim3((unsigned)tiles, ny), 1u << (K - FR), smem, st, A));
+    return launch_end(st);
+}
+
+template int fused_build<double2>(int, const std::vector<PrepOp>&, FusedPlan<double2>&);
+template int fused_build<float2>(int, const std::vector<PrepOp>&, FusedPlan<float2>&);
+template int fused_launch<double2>(const FusedPlan<double2>&, size_t, PassArgs<double2>&, unsigned, cudaStream_t);
+template int fused_launch<float2>(const FusedPlan<float2>&, size_t, PassArgs<float2>&, unsigned, cudaStream_t);
+
 template <typename V>
 static int run_fused(mera_state* s, const std::vector<PrepOp>& ops) {
-    const int n = s->n;
-    const int K = fused_tile_bits(s->dtype, n);
-    const int L = low_bits_for(s->dtype, K);
-    std::vector<Pass> passes = plan_passes(ops, n, K, L);
-    if (passes.empty()) return MERA_OK;
-    // opt in to the dynamic shared memory of a full tile (2^K elements)
-    const size_t tile_bytes = ((size_t)1 << K) * sizeof(V);
-    MERA_RETURN_IF(tile_bytes > 227 * 1024, MERA_EUNSUPPORTED, "tile of %zu bytes exceeds shared memory", tile_bytes);
-    const bool allow_i64 = sizeof(V) == 16;
-    // build every pass first: the diagonal tables go up in one copy
-    std::vector<PassArgs<V>> args(passes.size());
-    std::vector<unsigned char> eng(passes.size()), feat(passes.size());
-    std::vector<V> tabs;
-    for (size_t i = 0; i < passes.size(); ++i) {
-        if (passes[i].single >= 0) continue;
-        PassBuilder<V> b(args[i], tabs, ops, K, n);
-        MERA_TRY(b.build(passes[i], allow_i64));
-        eng[i] = b.i64 ? 1 : 0;
-        feat[i] = (unsigned char)round_feat(eng[i], b.features(), sizeof(V) == 16);
-    }
+    FusedPlan<V> plan;
+    MERA_TRY(fused_build<V>(s->n, ops, plan));
     const V* dtab = nullptr;
-    if (!tabs.empty()) {
-        const size_t bytes = tabs.size() * sizeof(V);
+    if (!plan.tabs.empty()) {
+        const size_t bytes = plan.tabs.size() * sizeof(V);
         if (s->prog_bytes < bytes) {
             MERA_CHECK_CUDA(cudaStreamSynchronize(s->stream));   // earlier passes may read the old tables
             if (s->prog) cudaFree(s->prog);
@@ -694,24 +734,18 @@ static int run_fused(mera_state* s, const std::vector<PrepOp>& ops) {
             s->prog_bytes = bytes;
         }
         // pageable source: the call returns once the host buffer was consumed
-        MERA_CHECK_CUDA(cudaMemcpyAsync(s->prog, tabs.data(), bytes, cudaMemcpyHostToDevice, s->stream));
+        MERA_CHECK_CUDA(cudaMemcpyAsync(s->prog, plan.tabs.data(), bytes, cudaMemcpyHostToDevice, s->stream));
         dtab = reinterpret_cast<const V*>(s->prog);
     }
-    const uint64_t tiles = 1ull << (n - K);
-    MERA_RETURN_IF(tiles > 0x7fffffffull, MERA_EUNSUPPORTED, "too many tiles");
-    for (size_t i = 0; i < passes.size(); ++i) {
-        if (passes[i].single >= 0) {
-            MERA_TRY(apply_prepared(s, ops[passes[i].single]));
+    for (size_t i = 0; i < plan.args.size(); ++i) {
+        if (plan.single[i] >= 0) {
+            MERA_TRY(apply_prepared(s, ops[plan.single[i]]));
             continue;
         }
-        PassArgs<V>& A = args[i];
+        PassArgs<V>& A = plan.args[i];
         A.psi = reinterpret_cast<V*>(s->data);
         A.tab = dtab;
-        const bool need_sm = A.nph > 1 || A.load_smem || A.store_smem;
-        const size_t smem = need_sm ? tile_bytes : 0;
-        launch_begin(s->stream, MERA_KCLASS_TILE, 2.0 * (double)num_amps(s) * sizeof(V));
-        MERA_TRY(launch_tile<V>(eng[i], feat[i], (unsigned)tiles, 1u << (K - FR), smem, s->stream, A));
-        MERA_TRY(launch_end(s->stream));
+        MERA_TRY(fused_launch<V>(plan, i, A, 1, s->stream));
     }
     return MERA_OK;
 }

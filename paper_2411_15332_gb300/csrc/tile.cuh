@@ -61,7 +61,7 @@ enum TileOpType : int8_t {
 
 struct TileOp {
     int8_t type;
-    int8_t a, b, c;      // register bits (a is the most significant sub-index bit; c unused)
+    int8_t a, b, c;      // register bits (a is the most significant sub-index bit); c: 1 = per-state coefficients
     int8_t nt;           // diag: number of targets; dsep: non-tile factors
     int8_t tq[3];        // diag: global target positions (tq[0] most significant)
     int32_t coef;        // first coefficient in PassArgs::coef
@@ -89,6 +89,13 @@ template <typename V>
 struct PassArgs {
     V* psi;
     const V* tab;        // separable-diagonal tables (device), 2^K entries each
+    // batches of states (blockIdx.y): state = psi + slot * bstride with
+    // slot = slots[blockIdx.y] (or blockIdx.y when slots is NULL); ops with
+    // c == 1 read their coefficients from bcoef + blockIdx.y * bcstride
+    const int* slots;
+    unsigned long long bstride;
+    const V* bcoef;
+    int bcstride;
     int K;               // tile bits
     int nph;             // phases
     int load_smem;       // 1: stage the first phase's load through shared memory
@@ -500,6 +507,8 @@ __global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
     const uint32_t tid = threadIdx.x;
     const uint64_t tile = blockIdx.x;
     const uint64_t tb = insert_zeros(tile, a.tpos, K);    // global index of local 0
+    SV* const psi = a.psi + (a.slots ? (unsigned long long)a.slots[blockIdx.y] : (unsigned long long)blockIdx.y) * a.bstride;
+    const V* const bcf = reinterpret_cast<const V*>(a.bcoef) + (size_t)blockIdx.y * a.bcstride;
     V x[FRA];
     int S = 0;   // ENG_I64: fixed-point exponent
 
@@ -514,7 +523,7 @@ __global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
         for (int r = 0; r < FR; ++r) st[r] = swz<EB>((int)(T << r));
         const int s0 = swz<EB>((int)tid);
 #pragma unroll
-        for (int i = 0; i < FRA; ++i) sms[s0 ^ dep4x(i, st)] = a.psi[gt | dep4(i, gtop)];
+        for (int i = 0; i < FRA; ++i) sms[s0 ^ dep4x(i, st)] = psi[gt | dep4(i, gtop)];
         __syncthreads();
     }
 
@@ -534,7 +543,7 @@ __global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
         if (p == 0) {
             if (!a.load_smem) {
 #pragma unroll
-                for (int j = 0; j < FRA; ++j) x[j] = raw_load<SV, V>(a.psi[gb | dep4(j, gm)]);
+                for (int j = 0; j < FRA; ++j) x[j] = raw_load<SV, V>(psi[gb | dep4(j, gm)]);
             } else {
 #pragma unroll
                 for (int j = 0; j < FRA; ++j) x[j] = raw_load<SV, V>(sms[sb ^ dep4x(j, sr)]);
@@ -565,7 +574,8 @@ __global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
         }
         for (int o = ph.op_begin; o < ph.op_end; ++o) {
             const TileOp& op = a.ops[o];
-            apply_tile_op<V, SV, FEAT>(x, op, a, reinterpret_cast<const V*>(a.coef) + op.coef, gb, gm, lb, lm);
+            const V* cf = (op.c ? bcf : reinterpret_cast<const V*>(a.coef)) + op.coef;
+            apply_tile_op<V, SV, FEAT>(x, op, a, cf, gb, gm, lb, lm);
         }
         if (p != a.nph - 1) {
             // each slot is read and written by its owner only within a phase
@@ -602,7 +612,7 @@ __global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
         }
         if (!a.store_smem) {
 #pragma unroll
-            for (int j = 0; j < FRA; ++j) a.psi[gb | dep4(j, gm)] = out[j];
+            for (int j = 0; j < FRA; ++j) psi[gb | dep4(j, gm)] = out[j];
         } else {
             // a thread rewrites only the slots it read itself in this phase
 #pragma unroll
@@ -617,7 +627,7 @@ __global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
             for (int r = 0; r < FR; ++r) st[r] = swz<EB>((int)(T << r));
             const int s0 = swz<EB>((int)tid);
 #pragma unroll
-            for (int i = 0; i < FRA; ++i) a.psi[gt | dep4(i, gtop)] = sms[s0 ^ dep4x(i, st)];
+            for (int i = 0; i < FRA; ++i) psi[gt | dep4(i, gtop)] = sms[s0 ^ dep4x(i, st)];
         }
     }
 }
