@@ -49,6 +49,8 @@ def _args():
     p.add_argument("--dtype", default="c128", choices=["c128", "c64"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-qnn", action="store_true")
+    p.add_argument("--qnn-requests", type=int, default=512)
     return p.parse_args()
 
 
@@ -207,6 +209,59 @@ print(json.dumps({"value": done / dt, "gates": g, "seconds": dt, "n": n}))
                        f"layered circuit family at n={d['n']} for {d['seconds']:.1f} s")}
 
 
+def _qnn_section(args):
+    """Secondary QNN measurements: the serving workload (a bounded prefix of
+    the 4096 seeded requests, n ~ U{8..20}, L ~ U{4..12}, complex64) served
+    with continuous batching vs one circuit at a time through the plain
+    single-state path, and adjoint training gradients (1024 circuits,
+    n = 16, 10 layers, 320 angles)."""
+    import numpy as np
+    import torch
+    import paper_2411_15332_gb300 as mera
+    from paper_2411_15332_gb300 import inputs
+    from paper_2411_15332_gb300.serve import Server, requests_from_workload
+    out = {}
+    reqs = inputs.qnn_requests(4096, seed=4)[: args.qnn_requests]
+    # plain: one circuit at a time (fused single-state path), a sample
+    sample = reqs[:64]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lat = []
+    for r in sample:
+        t1 = time.perf_counter()
+        st = mera.State(r["n"], "c64")
+        st.apply_circuit(inputs.ansatz_ops(r["n"], r["theta"]), mode="fused")
+        st.observables(0)
+        st.close()
+        lat.append(time.perf_counter() - t1)
+    plain_s = time.perf_counter() - t0
+    plain_rate = len(sample) / plain_s
+    out["plain"] = {"circuits_per_s": plain_rate, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                    "p99_ms": float(np.percentile(lat, 99) * 1e3), "sample": len(sample)}
+    # serving: saturation (all requests at t=0) and Poisson arrivals at 0.8x plain capacity... of the server
+    srv = Server(dtype="c64", mem_budget=64 << 30, slots_per_n=512)
+    srv.run(requests_from_workload(reqs))
+    sat = srv.stats()
+    rate = 0.8 * sat["circuits_per_s"]
+    srv2 = Server(dtype="c64", mem_budget=64 << 30, slots_per_n=512)
+    srv2.run(requests_from_workload(reqs, rate=rate))
+    poi = srv2.stats()
+    out["serving"] = {"requests": len(reqs), "saturation": sat,
+                      "poisson": dict(poi, rate_per_s=rate)}
+    # training: adjoint gradients of the 1024-circuit batch
+    theta = inputs.qnn_batch(1024, 16, 10, seed=5)
+    b = mera.Batch(16, 1024, "c64")
+    b.adjoint_grad(theta[:8])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.adjoint_grad(theta)
+    tr = time.perf_counter() - t0
+    out["training"] = {"circuits": 1024, "params_per_circuit": 320, "seconds": tr,
+                       "circuit_gradients_per_s": 1024 / tr, "dtype": "c64"}
+    b.close()
+    return out
+
+
 # ----------------------------------------------------------- arms ----------
 def run_reference(args, rank, world):
     if rank != 0:
@@ -327,6 +382,15 @@ def run_mera(args, rank, world, local_rank):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = _cpu_baseline()
+    qnn = None
+    if rank == 0 and world == 1 and not args.no_qnn and args.workload == "layered":
+        st.close()
+        st.tensor = None            # release the 16 GiB state before the QNN runs
+        torch.cuda.empty_cache()
+        try:
+            qnn = _qnn_section(args)
+        except Exception as ex:
+            qnn = {"error": str(ex)[:300]}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
@@ -339,7 +403,7 @@ def run_mera(args, rank, world, local_rank):
                            "l2": "state (%d GiB) larger than L2 (129 MB); no flush needed" % (((1 << n) * (16 if args.dtype == 'c128' else 8)) >> 30),
                            "readout": {"norm2": obs[0], "z0": obs[1]}},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-                "clocks": clocks, "kernel_classes": prof}
+                "clocks": clocks, "kernel_classes": prof, "qnn": qnn}
         print(json.dumps(line), flush=True)
     st.close()
 

@@ -94,6 +94,73 @@ static int coef_need(const PrepOp& P) {
 static void plan_segment(const std::vector<PrepOp>& ops, std::vector<int> remaining, int n, int K, int L,
                          std::vector<Pass>& passes);
 
+// A single-qubit diagonal gate (phase on one qubit) -- the kind folded into
+// a separable table.
+static int diag_qubit(const PrepOp& P) {
+    if (P.kind != KIND_DIAG || P.bslot >= 0) return -1;
+    if (P.k == 1 && P.cmask == 0) return P.t[0];
+    if (P.k == 0 && __builtin_popcountll(P.cmask) == 1) return __builtin_ctzll(P.cmask);
+    return -1;
+}
+
+// Move single-qubit diagonal gates whose qubit is not a tile bit of their
+// pass to the first later pass where it is, when no gate targeting that
+// qubit (non-diagonal) runs in between: the diagonal commutes with every
+// gate that does not target its qubit, and in a pass where the qubit is a
+// tile bit its factor comes from the pass's table instead of a per-tile
+// product.
+static void sink_diagonals(const std::vector<PrepOp>& ops, std::vector<Pass>& passes) {
+    const int np = (int)passes.size();
+    for (int i = 0; i < np; ++i) {
+        if (passes[i].single >= 0) continue;
+        std::vector<int> keep;
+        std::vector<std::pair<int, int>> moved;   // (op, target pass)
+        for (size_t k = 0; k < passes[i].ops.size(); ++k) {
+            const int idx = passes[i].ops[k];
+            const int q = diag_qubit(ops[idx]);
+            if (q < 0 || ((passes[i].tile_mask >> q) & 1ull)) {
+                keep.push_back(idx);
+                continue;
+            }
+            const uint64_t bit = 1ull << q;
+            bool blocked = false;
+            // later ops of this pass
+            for (size_t m = k + 1; m < passes[i].ops.size() && !blocked; ++m) {
+                const PrepOp& G = ops[passes[i].ops[m]];
+                if (G.kind != KIND_DIAG && (op_targets(G) & bit)) blocked = true;
+            }
+            int dest = -1;
+            for (int j = i + 1; j < np && !blocked; ++j) {
+                if (passes[j].single >= 0) {
+                    const PrepOp& G = ops[passes[j].single];
+                    if (op_targets(G) & bit) blocked = true;
+                    continue;
+                }
+                if ((passes[j].tile_mask >> q) & 1ull) {
+                    dest = j;
+                    break;
+                }
+                for (int m : passes[j].ops) {
+                    const PrepOp& G = ops[m];
+                    if (G.kind != KIND_DIAG && (op_targets(G) & bit)) {
+                        blocked = true;
+                        break;
+                    }
+                }
+            }
+            if (dest < 0 || blocked) {
+                keep.push_back(idx);
+                continue;
+            }
+            moved.push_back(std::make_pair(idx, dest));
+        }
+        passes[i].ops.swap(keep);
+        // insert at the front of the destination (before every op there)
+        for (auto it = moved.rbegin(); it != moved.rend(); ++it)
+            passes[it->second].ops.insert(passes[it->second].ops.begin(), it->first);
+    }
+}
+
 static std::vector<Pass> plan_passes(const std::vector<PrepOp>& ops, int n, int K, int L) {
     std::vector<Pass> passes;
     std::vector<int> seg;
@@ -110,6 +177,7 @@ static std::vector<Pass> plan_passes(const std::vector<PrepOp>& ops, int n, int 
         seg.push_back(i);
     }
     plan_segment(ops, seg, n, K, L, passes);
+    sink_diagonals(ops, passes);
     return passes;
 }
 
@@ -243,8 +311,99 @@ struct PassBuilder {
     int nop = 0, ncoef = 0, nz4 = 0, nnt = 0;
     bool i64 = false;
 
+    // The open separable-diagonal op: later diagonal runs fold into its
+    // table while only pure index permutations (X, CNOT, SWAP, Toffoli:
+    // monomials with all values 1) run in between -- D_B applied after a
+    // permutation P equals D_B(P(l)) applied before it.  Non-tile control
+    // bits of those permutations and non-tile diagonal qubits select one
+    // of at most 2^DSEP_SEL_BITS tables.
+    struct Factor {
+        int q;
+        cplx lam[2];
+    };
+    struct Run {
+        std::vector<Factor> fac;
+        std::vector<int> perms;   // permutation ops between the table op and this run
+    };
+    struct OpenTable {
+        bool open = false;
+        int opi = -1;
+        std::vector<int> selq;    // selection qubits (non-tile)
+        std::vector<Run> runs;
+        std::vector<int> perms;   // permutation ops since the table op
+    } ot;
+
     PassBuilder(PassArgs<V>& a, std::vector<V>& t, const std::vector<PrepOp>& o, int k, int nn)
         : A(a), tabs(t), ops(o), K(k), n(nn) {}
+
+    static bool pure_perm(const PrepOp& P) {
+        if (P.kind != KIND_MONO || P.bslot >= 0 || P.k > 2) return false;
+        for (int s = 0; s < (1 << P.k); ++s)
+            if (P.v[s] != cplx(1, 0)) return false;
+        return true;
+    }
+
+    // A non-diagonal gate joins the pass: the open table stays open only
+    // across pure permutations.
+    void note_gate(int idx) {
+        if (!ot.open) return;
+        if (pure_perm(ops[idx])) ot.perms.push_back(idx);
+        else ot.open = false;
+    }
+
+    // Bit of qubit q at local index l (local qubits) or from the selection
+    // index (selection qubits).
+    int bit_at(int q, uint32_t l, uint32_t sel, const std::vector<int>& selq) const {
+        if (local_of[q] >= 0) return (int)((l >> local_of[q]) & 1u);
+        for (size_t f = 0; f < selq.size(); ++f)
+            if (selq[f] == q) return (int)((sel >> f) & 1u);
+        return 0;
+    }
+
+    // Where the amplitude at local index l (tile selection sel) sits after
+    // the permutations perms.
+    uint32_t permute(uint32_t l, uint32_t sel, const std::vector<int>& perms, const std::vector<int>& selq) const {
+        for (int idx : perms) {
+            const PrepOp& P = ops[idx];
+            bool on = true;
+            for (int q = 0; q < n && on; ++q)
+                if ((P.cmask >> q) & 1ull) on = bit_at(q, l, sel, selq) == (int)((P.cvals >> q) & 1ull);
+            if (!on) continue;
+            int s = 0;
+            for (int j = 0; j < P.k; ++j) s = (s << 1) | (int)((l >> local_of[P.t[j]]) & 1u);
+            int r = 0;   // the row that reads column s
+            for (int rr = 0; rr < (1 << P.k); ++rr)
+                if (P.perm[rr] == s) r = rr;
+            for (int j = 0; j < P.k; ++j) {
+                const uint32_t b = 1u << local_of[P.t[j]];
+                l = ((r >> (P.k - 1 - j)) & 1) ? (l | b) : (l & ~b);
+            }
+        }
+        return l;
+    }
+
+    // (Re)write the open table: T[sel][l] = prod over runs and their factors.
+    int write_table() {
+        TileOp& o = A.ops[ot.opi];
+        const size_t T = (size_t)1 << K;
+        const int nsel = (int)ot.selq.size();
+        MERA_RETURN_IF(nnt + nsel > TILE_MAX_NT, MERA_EUNSUPPORTED, "too many table selection qubits");
+        o.aux2 = nnt;
+        for (int q : ot.selq) A.ntq[nnt++] = (int8_t)q;
+        o.nt = (int8_t)nsel;
+        o.aux = (int)tabs.size();
+        tabs.resize(tabs.size() + (T << nsel));
+        for (uint32_t sel = 0; sel < (1u << nsel); ++sel)
+            for (uint32_t l = 0; l < T; ++l) {
+                cplx d = 1;
+                for (const Run& r : ot.runs) {
+                    const uint32_t pl = r.perms.empty() ? l : permute(l, sel, r.perms, ot.selq);
+                    for (const Factor& fc : r.fac) d *= fc.lam[bit_at(fc.q, pl, sel, ot.selq)];
+                }
+                tabs[o.aux + ((size_t)sel << K) + l] = enc<V>(d, i64);
+            }
+        return MERA_OK;
+    }
 
     int add_op(TileOp** out) {
         MERA_RETURN_IF(nop >= TILE_MAX_OPS, MERA_EUNSUPPORTED, "tile pass op table full");
@@ -324,42 +483,75 @@ struct PassBuilder {
             for (const Z4Term& z : terms) A.z4[nz4++] = z;
         }
         if (general) {
-            // table over the tile-local qubits (times lam[0] of every other
-            // qubit); the first DSEP_SEL_BITS non-tile qubits select one of
-            // 2^m tables pre-multiplied by lam[1]/lam[0] where their bit is 1,
-            // further non-tile factors are applied per tile
-            TileOp* o;
-            MERA_TRY(add_op(&o));
-            o->type = TOP_DSEP;
-            o->aux = (int)tabs.size();
-            o->aux2 = nnt;
-            cplx base = 1;
-            std::vector<cplx> rho;
+            std::vector<Factor> fac;
+            std::vector<int> nontile;
             for (int q = 0; q < n; ++q) {
-                if (!has[q] || local_of[q] >= 0) continue;
-                base *= lam[q][0];
-                MERA_RETURN_IF(nnt >= TILE_MAX_NT, MERA_EUNSUPPORTED, "too many non-tile diagonal factors");
-                A.ntq[nnt++] = (int8_t)q;
-                rho.push_back(lam[q][1] / lam[q][0]);
+                if (!has[q]) continue;
+                fac.push_back(Factor{q, {lam[q][0], lam[q][1]}});
+                if (local_of[q] < 0) nontile.push_back(q);
             }
-            const int nf = (int)rho.size();
-            const int nsel = std::min(nf, DSEP_SEL_BITS);
-            for (int f = nsel; f < nf; ++f) MERA_TRY(add_coef(rho[f]));
-            o->nt = (int8_t)nf;
-            const size_t T = (size_t)1 << K;
-            const size_t off = tabs.size();
-            tabs.resize(off + (T << nsel));
-            for (size_t sel = 0; sel < ((size_t)1 << nsel); ++sel) {
-                cplx b = base;
-                for (int f = 0; f < nsel; ++f)
-                    if ((sel >> f) & 1) b *= rho[f];
-                for (size_t l = 0; l < T; ++l) {
-                    cplx d = b;
-                    for (int j = 0; j < K; ++j) {
-                        const int q = A.tpos[j];
-                        if (has[q]) d *= lam[q][(l >> j) & 1];
+            if (ot.open) {
+                std::vector<int> sel = ot.selq;
+                auto add_sel = [&](int q) {
+                    if (local_of[q] < 0 && std::find(sel.begin(), sel.end(), q) == sel.end()) sel.push_back(q);
+                };
+                for (int q : nontile) add_sel(q);
+                for (int idx : ot.perms)
+                    for (int q = 0; q < n; ++q)
+                        if ((ops[idx].cmask >> q) & 1ull) add_sel(q);
+                if ((int)sel.size() <= DSEP_SEL_BITS) {
+                    ot.selq = sel;
+                    ot.runs.push_back(Run{fac, ot.perms});
+                    MERA_TRY(write_table());
+                    fac.clear();
+                }
+            }
+            if (!fac.empty()) {
+                TileOp* o;
+                MERA_TRY(add_op(&o));
+                o->type = TOP_DSEP;
+                if ((int)nontile.size() <= DSEP_SEL_BITS) {
+                    ot = OpenTable();
+                    ot.open = true;
+                    ot.opi = (int)(o - A.ops);
+                    ot.selq = nontile;
+                    ot.runs.push_back(Run{fac, {}});
+                    MERA_TRY(write_table());
+                } else {
+                    // more non-tile qubits than selection bits: the first
+                    // DSEP_SEL_BITS select a table, the rest multiply per tile
+                    ot.open = false;
+                    o->aux = (int)tabs.size();
+                    o->aux2 = nnt;
+                    cplx base = 1;
+                    std::vector<cplx> rho;
+                    for (int q : nontile) {
+                        base *= lam[q][0];
+                        MERA_RETURN_IF(nnt >= TILE_MAX_NT, MERA_EUNSUPPORTED, "too many non-tile diagonal factors");
+                        A.ntq[nnt++] = (int8_t)q;
+                        rho.push_back(lam[q][1] / lam[q][0]);
                     }
-                    tabs[off + (sel << K) + l] = enc<V>(d, i64);
+                    const int nf = (int)rho.size();
+                    const int nsel = std::min(nf, DSEP_SEL_BITS);
+                    o->coef = ncoef;
+                    for (int f2 = nsel; f2 < nf; ++f2) MERA_TRY(add_coef(rho[f2]));
+                    o->nt = (int8_t)nf;
+                    const size_t T = (size_t)1 << K;
+                    const size_t off = tabs.size();
+                    tabs.resize(off + (T << nsel));
+                    for (size_t sel = 0; sel < ((size_t)1 << nsel); ++sel) {
+                        cplx b = base;
+                        for (int f2 = 0; f2 < nsel; ++f2)
+                            if ((sel >> f2) & 1) b *= rho[f2];
+                        for (size_t l = 0; l < T; ++l) {
+                            cplx d = b;
+                            for (int j = 0; j < K; ++j) {
+                                const int q = A.tpos[j];
+                                if (has[q]) d *= lam[q][(l >> j) & 1];
+                            }
+                            tabs[off + (sel << K) + l] = enc<V>(d, i64);
+                        }
+                    }
                 }
             }
         }
@@ -396,12 +588,11 @@ struct PassBuilder {
                 o->coef = P.bslot * 4;
             } else if (P.is_h) {
                 o->type = TOP_H;
-            } else if (P.kind == KIND_MONO) {
+            } else if (P.kind == KIND_MONO && P.v[0] == cplx(1, 0) && P.v[1] == cplx(1, 0)) {
+                o->type = TOP_G1SWAP;
+            } else if (P.kind == KIND_MONO && phase_code_f(P.v[0]) <= 3 && phase_code_f(P.v[1]) <= 3) {
                 o->type = TOP_G1MONO;
-                for (int s2 = 0; s2 < 2; ++s2) {
-                    MERA_TRY(add_coef(P.v[s2]));
-                    o->codes |= (uint32_t)phase_code_f(P.v[s2]) << (3 * s2);
-                }
+                for (int s2 = 0; s2 < 2; ++s2) o->codes |= (uint32_t)phase_code_f(P.v[s2]) << (3 * s2);
             } else {
                 o->type = TOP_G1;
                 for (int s2 = 0; s2 < 4; ++s2) MERA_TRY(add_coef(P.m[s2]));
@@ -426,7 +617,9 @@ struct PassBuilder {
         int inv[8];
         for (int sr = 0; sr < (1 << k); ++sr) inv[conv(sr)] = sr;
         const int d = 1 << k;
-        if (P.kind == KIND_MONO) {
+        bool unit = P.kind == KIND_MONO;
+        for (int s2 = 0; unit && s2 < d; ++s2) unit = phase_code_f(P.v[s2]) <= 3;
+        if (unit) {
             o->type = TOP_G2MONO;
             for (int sr = 0; sr < d; ++sr) {
                 const int sg = conv(sr);
@@ -585,6 +778,7 @@ struct PassBuilder {
                 }
                 MERA_TRY(flush_diag(run));
                 run.clear();
+                note_gate(p.ops[i]);
                 MERA_TRY(add_gate(P, reg_of));
             }
             MERA_TRY(flush_diag(run));
@@ -770,14 +964,14 @@ static int describe_fused(int n, int dtype, const std::vector<PrepOp>& ops, std:
         }
         PassBuilder<V> b(A, tabs, ops, K, n);
         MERA_TRY(b.build(passes[i], sizeof(V) == 16));
-        int cnt[10] = {0};
+        int cnt[16] = {0};
         for (int o = 0; o < b.nop; ++o) cnt[A.ops[o].type]++;
         std::string bits;
         for (int j = 0; j < K; ++j) bits += std::to_string(A.tpos[j]) + (j + 1 < K ? "," : "");
         snprintf(line, sizeof(line),
                  "pass %zu: eng=%s nh=%d phases=%d ops=%d [g1=%d mono=%d h=%d g2=%d diag=%d dsep=%d z4=%d] "
                  "guard=%d load_smem=%d store_smem=%d tile={%s}\n",
-                 i, b.i64 ? "i64" : "fp", A.nh, A.nph, b.nop, cnt[TOP_G1], cnt[TOP_G1MONO] + cnt[TOP_G2MONO], cnt[TOP_H],
+                 i, b.i64 ? "i64" : "fp", A.nh, A.nph, b.nop, cnt[TOP_G1], cnt[TOP_G1MONO] + cnt[TOP_G2MONO] + cnt[TOP_G1SWAP], cnt[TOP_H],
                  cnt[TOP_G2], cnt[TOP_DIAG], cnt[TOP_DSEP], cnt[TOP_Z4], A.guard, A.load_smem, A.store_smem, bits.c_str());
         *out += line;
     }

@@ -53,7 +53,8 @@ enum TileOpType : int8_t {
     TOP_H = 2,        // unscaled Hadamard butterfly (pass scale at the end)
     TOP_G2 = 3,       // dense 4x4 on register bits a > b
     TOP_G2MONO = 4,   // monomial 4x4: row s takes phase(s) * amp perm(s)
-    // 5, 6: unused (three-target gates run as per-gate kernels between passes)
+    TOP_G1SWAP = 5,   // swap of the pair (X, CNOT, Toffoli): moves only
+    // 6: unused (three-target gates run as per-gate kernels between passes)
     TOP_DIAG = 7,     // diagonal on any bits: amp *= v[sub] where flagged
     TOP_DSEP = 8,     // separable diagonal: amp *= tab[local index] * prod(non-tile factors)
     TOP_Z4 = 9,       // product of exact phases i^e over pattern terms
@@ -256,16 +257,31 @@ template <typename V, int B>
 __device__ __forceinline__ void op_g1mono(V (&x)[FRA], const TileOp& o, const V* cf, uint64_t gb, const uint64_t* gm) {
     const uint32_t act = active16(o.cmask, o.cvals, gb, gm);
     if (act == 0) return;
-    const int c0 = code_at(o.codes, 0), c1 = code_at(o.codes, 1);
-    const V v0 = cf[0], v1 = cf[1];
+    // phases are unit codes here (the planner sends other monomials to G1)
+    const int c0 = code_at(o.codes, 0) & 3, c1 = code_at(o.codes, 1) & 3;
 #pragma unroll
     for (int j = 0; j < FRA; ++j) {
         if (j & (1 << B)) continue;
         const int j1 = j | (1 << B);
         if (!(act & (1u << j))) continue;
         const V a0 = x[j], a1 = x[j1];
-        x[j] = phase_any(c0, v0, a1);
-        x[j1] = phase_any(c1, v1, a0);
+        x[j] = mul_ik(a1, c0);
+        x[j1] = mul_ik(a0, c1);
+    }
+}
+
+template <typename V, int B>
+__device__ __forceinline__ void op_g1swap(V (&x)[FRA], const TileOp& o, uint64_t gb, const uint64_t* gm) {
+    const uint32_t act = active16(o.cmask, o.cvals, gb, gm);
+    if (act == 0) return;
+#pragma unroll
+    for (int j = 0; j < FRA; ++j) {
+        if (j & (1 << B)) continue;
+        const int j1 = j | (1 << B);
+        if (!(act & (1u << j))) continue;
+        const V t = x[j];
+        x[j] = x[j1];
+        x[j1] = t;
     }
 }
 
@@ -302,7 +318,7 @@ __device__ __forceinline__ void op_g2(V (&x)[FRA], const TileOp& o, const V* cf,
 #pragma unroll
                 for (int u = 1; u < 4; ++u)
                     if (src == u) v = in[u];
-                x[id[s]] = phase_any(code_at(o.codes, s), cf[s], v);
+                x[id[s]] = mul_ik(v, code_at(o.codes, s) & 3);
             }
         } else {
 #pragma unroll
@@ -398,6 +414,14 @@ __device__ __forceinline__ void apply_tile_op(V (&x)[FRA], const TileOp& o, cons
         case 1: op_g1mono<V, 1>(x, o, cf, gb, gm); break;
         case 2: op_g1mono<V, 2>(x, o, cf, gb, gm); break;
         default: op_g1mono<V, 3>(x, o, cf, gb, gm); break;
+        }
+        break;
+    case TOP_G1SWAP:
+        switch (o.a) {
+        case 0: op_g1swap<V, 0>(x, o, gb, gm); break;
+        case 1: op_g1swap<V, 1>(x, o, gb, gm); break;
+        case 2: op_g1swap<V, 2>(x, o, gb, gm); break;
+        default: op_g1swap<V, 3>(x, o, gb, gm); break;
         }
         break;
     case TOP_H:
@@ -523,7 +547,7 @@ __global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
         for (int r = 0; r < FR; ++r) st[r] = swz<EB>((int)(T << r));
         const int s0 = swz<EB>((int)tid);
 #pragma unroll
-        for (int i = 0; i < FRA; ++i) sms[s0 ^ dep4x(i, st)] = psi[gt | dep4(i, gtop)];
+        for (int i = 0; i < FRA; ++i) sms[s0 ^ dep4x(i, st)] = __ldcs(psi + (gt | dep4(i, gtop)));
         __syncthreads();
     }
 
@@ -543,7 +567,7 @@ __global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
         if (p == 0) {
             if (!a.load_smem) {
 #pragma unroll
-                for (int j = 0; j < FRA; ++j) x[j] = raw_load<SV, V>(psi[gb | dep4(j, gm)]);
+                for (int j = 0; j < FRA; ++j) x[j] = raw_load<SV, V>(__ldcs(psi + (gb | dep4(j, gm))));
             } else {
 #pragma unroll
                 for (int j = 0; j < FRA; ++j) x[j] = raw_load<SV, V>(sms[sb ^ dep4x(j, sr)]);
@@ -612,7 +636,7 @@ __global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
         }
         if (!a.store_smem) {
 #pragma unroll
-            for (int j = 0; j < FRA; ++j) psi[gb | dep4(j, gm)] = out[j];
+            for (int j = 0; j < FRA; ++j) __stcs(psi + (gb | dep4(j, gm)), out[j]);
         } else {
             // a thread rewrites only the slots it read itself in this phase
 #pragma unroll
@@ -627,7 +651,7 @@ __global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
             for (int r = 0; r < FR; ++r) st[r] = swz<EB>((int)(T << r));
             const int s0 = swz<EB>((int)tid);
 #pragma unroll
-            for (int i = 0; i < FRA; ++i) psi[gt | dep4(i, gtop)] = sms[s0 ^ dep4x(i, st)];
+            for (int i = 0; i < FRA; ++i) __stcs(psi + (gt | dep4(i, gtop)), sms[s0 ^ dep4x(i, st)]);
         }
     }
 }
