@@ -246,6 +246,7 @@ int mera_state_destroy(mera_state* s) {
     if (s->scratch) cudaFree(s->scratch);
     if (s->prog) cudaFree(s->prog);
     if (s->prog_host) cudaFreeHost(s->prog_host);
+    fused_cache_free(s);
     delete s;
     return MERA_OK;
     API_END
@@ -375,6 +376,7 @@ int mera_apply_circuit(mera_state* s, const mera_op* ops, size_t nops, int mode)
     MERA_TRY(check_state(s));
     MERA_RETURN_IF(nops > 0 && ops == nullptr, MERA_EINVAL, "ops is NULL");
     MERA_RETURN_IF(mode != MERA_MODE_PER_GATE && mode != MERA_MODE_FUSED, MERA_EINVAL, "unknown mode %d", mode);
+    if (mode == MERA_MODE_FUSED) return apply_fused_circuit(s, ops, nops);
     std::vector<PrepOp> prep(nops);
     for (size_t j = 0; j < nops; ++j) {
         int st = prepare_op(ops[j], s->n, &prep[j]);
@@ -384,11 +386,8 @@ int mera_apply_circuit(mera_state* s, const mera_op* ops, size_t nops, int mode)
             return st;
         }
     }
-    if (mode == MERA_MODE_PER_GATE) {
-        for (const PrepOp& P : prep) MERA_TRY(apply_prepared(s, P));
-        return MERA_OK;
-    }
-    return apply_fused(s, prep);
+    for (const PrepOp& P : prep) MERA_TRY(apply_prepared(s, P));
+    return MERA_OK;
     API_END
 }
 

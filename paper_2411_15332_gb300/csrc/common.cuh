@@ -74,6 +74,9 @@ struct mera_state {
     size_t prog_bytes = 0;
     void* prog_host = nullptr;  // pinned staging of programs
     size_t prog_host_bytes = 0;
+    // last fused circuit: its key (the raw ops) and its built passes, whose
+    // diagonal tables are resident in `prog`
+    void* fused_cache = nullptr;
 };
 
 namespace mera {
@@ -114,6 +117,10 @@ int gate_matrix(int gate, const double* params, int* nt, cplx* out);
 int apply_prepared(mera_state* s, const PrepOp& op);
 // Fused path (fused.cu).
 int apply_fused(mera_state* s, const std::vector<PrepOp>& ops);
+// Fused path for a raw op list: a circuit identical to the previous fused
+// circuit of the state reuses its passes and device tables.
+int apply_fused_circuit(mera_state* s, const mera_op* ops, size_t nops);
+void fused_cache_free(mera_state* s);
 int plan_summary(int n, int dtype, const std::vector<PrepOp>& ops, std::string* out, int* npasses);
 
 }  // namespace mera

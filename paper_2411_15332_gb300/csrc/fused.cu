@@ -79,9 +79,10 @@ static bool op_is_exact(const PrepOp& P) {
     return true;
 }
 
-// Passes with at least this many Hadamard levels keep only exact gates (the
-// int64 engine); other gates wait for the next pass.
-static constexpr int I64_MIN_H = 3;
+
+// Passes with at least this many Hadamard levels take exact gates only;
+// other gates wait for the next pass.
+static constexpr int H_HEAVY = 3;
 
 static int coef_need(const PrepOp& P) {
     if (P.bslot >= 0) return 0;
@@ -199,7 +200,9 @@ static void plan_segment(const std::vector<PrepOp>& ops, std::vector<int> remain
             const PrepOp& P = ops[idx];
             const uint64_t q = op_qubits(P);
             bool take = !(q & blocked);
-            if (take && !op_is_exact(P) && nh >= I64_MIN_H) take = false;
+            // Hadamard-heavy passes keep to exact gates (butterflies, moves,
+            // unit phases): their kernel variant stays lean
+            if (take && !op_is_exact(P) && nh >= H_HEAVY) take = false;
             if (take && (nops + 1 > TILE_MAX_OPS || ncoef + coef_need(P) > TILE_MAX_COEF)) take = false;
             if (take && P.kind != KIND_DIAG) {
                 const uint64_t t = op_targets(P);
@@ -310,6 +313,7 @@ struct PassBuilder {
     int local_of[64];
     int nop = 0, ncoef = 0, nz4 = 0, nnt = 0;
     bool i64 = false;
+    bool fp_only = false;   // keep every pass in the float engine
 
     // The open separable-diagonal op: later diagonal runs fold into its
     // table while only pure index permutations (X, CNOT, SWAP, Toffoli:
@@ -324,6 +328,7 @@ struct PassBuilder {
     struct Run {
         std::vector<Factor> fac;
         std::vector<int> perms;   // permutation ops between the table op and this run
+        std::vector<Z4Term> z4;   // unit-phase patterns folded into the table
     };
     struct OpenTable {
         bool open = false;
@@ -393,14 +398,42 @@ struct PassBuilder {
         o.nt = (int8_t)nsel;
         o.aux = (int)tabs.size();
         tabs.resize(tabs.size() + (T << nsel));
+        // folded patterns as (local mask, local values, selection mask, selection values)
+        struct Pat {
+            uint32_t lm, lv, sm, sv;
+            int e;
+        };
+        std::vector<std::vector<Pat>> pats(ot.runs.size());
+        for (size_t ri = 0; ri < ot.runs.size(); ++ri)
+            for (const Z4Term& z : ot.runs[ri].z4) {
+                Pat pt{0, 0, 0, 0, z.e};
+                for (int q = 0; q < n; ++q) {
+                    if (!((z.mask >> q) & 1ull)) continue;
+                    const uint32_t v = (uint32_t)((z.vals >> q) & 1ull);
+                    if (local_of[q] >= 0) {
+                        pt.lm |= 1u << local_of[q];
+                        pt.lv |= v << local_of[q];
+                    } else {
+                        const int f = (int)(std::find(ot.selq.begin(), ot.selq.end(), q) - ot.selq.begin());
+                        pt.sm |= 1u << f;
+                        pt.sv |= v << f;
+                    }
+                }
+                pats[ri].push_back(pt);
+            }
+        static const cplx ipow[4] = {cplx(1, 0), cplx(0, 1), cplx(-1, 0), cplx(0, -1)};
         for (uint32_t sel = 0; sel < (1u << nsel); ++sel)
             for (uint32_t l = 0; l < T; ++l) {
                 cplx d = 1;
-                for (const Run& r : ot.runs) {
+                int e = 0;
+                for (size_t ri = 0; ri < ot.runs.size(); ++ri) {
+                    const Run& r = ot.runs[ri];
                     const uint32_t pl = r.perms.empty() ? l : permute(l, sel, r.perms, ot.selq);
                     for (const Factor& fc : r.fac) d *= fc.lam[bit_at(fc.q, pl, sel, ot.selq)];
+                    for (const Pat& pt : pats[ri])
+                        if ((pl & pt.lm) == pt.lv && (sel & pt.sm) == pt.sv) e += pt.e;
                 }
-                tabs[o.aux + ((size_t)sel << K) + l] = enc<V>(d, i64);
+                tabs[o.aux + ((size_t)sel << K) + l] = enc<V>(d * ipow[e & 3], tq62());
             }
         return MERA_OK;
     }
@@ -412,11 +445,15 @@ struct PassBuilder {
         (*out)->coef = ncoef;
         return MERA_OK;
     }
-    int add_coef(cplx c) {
+    int add_coef(cplx c) { return add_coef(c, i64); }
+    int add_coef(cplx c, bool q62) {
         MERA_RETURN_IF(ncoef >= TILE_MAX_COEF, MERA_EUNSUPPORTED, "tile pass coefficient table full");
-        A.coef[ncoef++] = enc<V>(c, i64);
+        A.coef[ncoef++] = enc<V>(c, q62);
         return MERA_OK;
     }
+    // complex128 separable-diagonal tables and their per-tile factors are
+    // Q62 fixed point in both engines (integer multiplies)
+    bool tq62() const { return sizeof(V) == 16; }
 
     // A run of diagonal gates (they commute): single-qubit factors become one
     // separable diagonal (or exact Z4 terms when all are unit phases), unit-
@@ -459,7 +496,110 @@ struct PassBuilder {
         bool general = false;
         for (int q = 0; q < n; ++q)
             if (has[q] && (phase_code_f(lam[q][0]) > 3 || phase_code_f(lam[q][1]) > 3)) general = true;
-        if (!general) {
+        std::vector<Factor> fac;
+        std::vector<int> nontile;
+        for (int q = 0; q < n; ++q) {
+            if (!has[q]) continue;
+            fac.push_back(Factor{q, {lam[q][0], lam[q][1]}});
+            if (local_of[q] < 0) nontile.push_back(q);
+        }
+        // unit-phase patterns whose non-tile qubits fit the selection bits
+        // fold into the table as well (the table multiply happens anyway)
+        auto fold_terms = [&](std::vector<int>& sel, std::vector<Z4Term>& keep) {
+            std::vector<Z4Term> folded;
+            for (const Z4Term& z : terms) {
+                std::vector<int> s2 = sel;
+                bool ok = true;
+                for (int q = 0; q < n && ok; ++q) {
+                    if (!((z.mask >> q) & 1ull) || local_of[q] >= 0) continue;
+                    if (std::find(s2.begin(), s2.end(), q) != s2.end()) continue;
+                    if ((int)s2.size() >= DSEP_SEL_BITS) ok = false;
+                    else s2.push_back(q);
+                }
+                if (ok) {
+                    sel = s2;
+                    folded.push_back(z);
+                } else {
+                    keep.push_back(z);
+                }
+            }
+            return folded;
+        };
+        std::vector<Z4Term> rest = terms;
+        bool folded = false;
+        if (ot.open && (!fac.empty() || !terms.empty())) {
+            std::vector<int> sel = ot.selq;
+            auto add_sel = [&](int q) {
+                if (local_of[q] < 0 && std::find(sel.begin(), sel.end(), q) == sel.end()) sel.push_back(q);
+            };
+            for (int q : nontile) add_sel(q);
+            for (int idx : ot.perms)
+                for (int q = 0; q < n; ++q)
+                    if ((ops[idx].cmask >> q) & 1ull) add_sel(q);
+            if ((int)sel.size() <= DSEP_SEL_BITS) {
+                std::vector<Z4Term> keep;
+                std::vector<Z4Term> ft = fold_terms(sel, keep);
+                ot.selq = sel;
+                ot.runs.push_back(Run{fac, ot.perms, ft});
+                MERA_TRY(write_table());
+                rest = keep;
+                folded = true;
+            }
+        }
+        if (!folded && general) {
+            TileOp* o;
+            MERA_TRY(add_op(&o));
+            o->type = TOP_DSEP;
+            folded = true;
+            if ((int)nontile.size() <= DSEP_SEL_BITS) {
+                ot = OpenTable();
+                ot.open = true;
+                ot.opi = (int)(o - A.ops);
+                ot.selq = nontile;
+                std::vector<Z4Term> keep;
+                std::vector<Z4Term> ft = fold_terms(ot.selq, keep);
+                ot.runs.push_back(Run{fac, {}, ft});
+                MERA_TRY(write_table());
+                rest = keep;
+            } else {
+                // more non-tile qubits than selection bits: the first
+                // DSEP_SEL_BITS select a table, the rest multiply per tile
+                ot.open = false;
+                o->aux = (int)tabs.size();
+                o->aux2 = nnt;
+                cplx base = 1;
+                std::vector<cplx> rho;
+                for (int q : nontile) {
+                    base *= lam[q][0];
+                    MERA_RETURN_IF(nnt >= TILE_MAX_NT, MERA_EUNSUPPORTED, "too many non-tile diagonal factors");
+                    A.ntq[nnt++] = (int8_t)q;
+                    rho.push_back(lam[q][1] / lam[q][0]);
+                }
+                const int nf = (int)rho.size();
+                const int nsel = std::min(nf, DSEP_SEL_BITS);
+                o->coef = ncoef;
+                for (int f2 = nsel; f2 < nf; ++f2) MERA_TRY(add_coef(rho[f2], tq62()));
+                o->nt = (int8_t)nf;
+                const size_t T = (size_t)1 << K;
+                const size_t off = tabs.size();
+                tabs.resize(off + (T << nsel));
+                for (size_t sel = 0; sel < ((size_t)1 << nsel); ++sel) {
+                    cplx b = base;
+                    for (int f2 = 0; f2 < nsel; ++f2)
+                        if ((sel >> f2) & 1) b *= rho[f2];
+                    for (size_t l = 0; l < T; ++l) {
+                        cplx d = b;
+                        for (int j = 0; j < K; ++j) {
+                            const int q = A.tpos[j];
+                            if (has[q]) d *= lam[q][(l >> j) & 1];
+                        }
+                        tabs[off + (sel << K) + l] = enc<V>(d, tq62());
+                    }
+                }
+            }
+        }
+        if (!folded) {
+            // unit phases only and no table to join: exact sign / i terms
             for (int q = 0; q < n; ++q) {
                 if (!has[q]) continue;
                 for (int b = 0; b < 2; ++b) {
@@ -469,91 +609,18 @@ struct PassBuilder {
                     z.mask = 1ull << q;
                     z.vals = b ? (1ull << q) : 0ull;
                     z.e = (int)e;
-                    terms.push_back(z);
+                    rest.push_back(z);
                 }
             }
         }
-        if (!terms.empty()) {
-            MERA_RETURN_IF(nz4 + (int)terms.size() > TILE_MAX_Z4, MERA_EUNSUPPORTED, "too many sign terms");
+        if (!rest.empty()) {
+            MERA_RETURN_IF(nz4 + (int)rest.size() > TILE_MAX_Z4, MERA_EUNSUPPORTED, "too many sign terms");
             TileOp* o;
             MERA_TRY(add_op(&o));
             o->type = TOP_Z4;
             o->aux = nz4;
-            o->aux2 = (int)terms.size();
-            for (const Z4Term& z : terms) A.z4[nz4++] = z;
-        }
-        if (general) {
-            std::vector<Factor> fac;
-            std::vector<int> nontile;
-            for (int q = 0; q < n; ++q) {
-                if (!has[q]) continue;
-                fac.push_back(Factor{q, {lam[q][0], lam[q][1]}});
-                if (local_of[q] < 0) nontile.push_back(q);
-            }
-            if (ot.open) {
-                std::vector<int> sel = ot.selq;
-                auto add_sel = [&](int q) {
-                    if (local_of[q] < 0 && std::find(sel.begin(), sel.end(), q) == sel.end()) sel.push_back(q);
-                };
-                for (int q : nontile) add_sel(q);
-                for (int idx : ot.perms)
-                    for (int q = 0; q < n; ++q)
-                        if ((ops[idx].cmask >> q) & 1ull) add_sel(q);
-                if ((int)sel.size() <= DSEP_SEL_BITS) {
-                    ot.selq = sel;
-                    ot.runs.push_back(Run{fac, ot.perms});
-                    MERA_TRY(write_table());
-                    fac.clear();
-                }
-            }
-            if (!fac.empty()) {
-                TileOp* o;
-                MERA_TRY(add_op(&o));
-                o->type = TOP_DSEP;
-                if ((int)nontile.size() <= DSEP_SEL_BITS) {
-                    ot = OpenTable();
-                    ot.open = true;
-                    ot.opi = (int)(o - A.ops);
-                    ot.selq = nontile;
-                    ot.runs.push_back(Run{fac, {}});
-                    MERA_TRY(write_table());
-                } else {
-                    // more non-tile qubits than selection bits: the first
-                    // DSEP_SEL_BITS select a table, the rest multiply per tile
-                    ot.open = false;
-                    o->aux = (int)tabs.size();
-                    o->aux2 = nnt;
-                    cplx base = 1;
-                    std::vector<cplx> rho;
-                    for (int q : nontile) {
-                        base *= lam[q][0];
-                        MERA_RETURN_IF(nnt >= TILE_MAX_NT, MERA_EUNSUPPORTED, "too many non-tile diagonal factors");
-                        A.ntq[nnt++] = (int8_t)q;
-                        rho.push_back(lam[q][1] / lam[q][0]);
-                    }
-                    const int nf = (int)rho.size();
-                    const int nsel = std::min(nf, DSEP_SEL_BITS);
-                    o->coef = ncoef;
-                    for (int f2 = nsel; f2 < nf; ++f2) MERA_TRY(add_coef(rho[f2]));
-                    o->nt = (int8_t)nf;
-                    const size_t T = (size_t)1 << K;
-                    const size_t off = tabs.size();
-                    tabs.resize(off + (T << nsel));
-                    for (size_t sel = 0; sel < ((size_t)1 << nsel); ++sel) {
-                        cplx b = base;
-                        for (int f2 = 0; f2 < nsel; ++f2)
-                            if ((sel >> f2) & 1) b *= rho[f2];
-                        for (size_t l = 0; l < T; ++l) {
-                            cplx d = b;
-                            for (int j = 0; j < K; ++j) {
-                                const int q = A.tpos[j];
-                                if (has[q]) d *= lam[q][(l >> j) & 1];
-                            }
-                            tabs[off + (sel << K) + l] = enc<V>(d, i64);
-                        }
-                    }
-                }
-            }
+            o->aux2 = (int)rest.size();
+            for (const Z4Term& z : rest) A.z4[nz4++] = z;
         }
         for (int idx : others) {
             const PrepOp& P = ops[idx];
@@ -661,10 +728,6 @@ struct PassBuilder {
                 A.tpos[j] = q;
                 local_of[q] = j++;
             }
-        // engine: complex128 passes with at least I64_MIN_H Hadamard levels run
-        // the int64 engine (exact integer butterflies); the others stay in
-        // float64, where moves and sign flips are exact and a folded diagonal
-        // run costs one complex multiply per amplitude
         int nh = 0;
         bool all_unitary = true;
         double gain_bits = 0.0;
@@ -683,7 +746,11 @@ struct PassBuilder {
         A.nh = nh;
         bool exact = true;
         for (int idx : p.ops) exact = exact && op_is_exact(ops[idx]);
-        i64 = allow_i64 && exact && nh >= I64_MIN_H;
+        // FP64 issues about one operation per clock per SM on GB300, so
+        // complex128 passes with butterflies run the int64 engine; the
+        // others stay in float64 storage, where moves and sign flips are
+        // exact and table multiplies run in integer arithmetic
+        i64 = allow_i64 && !fp_only && nh > 0;
         A.scale = std::pow(0.5, nh / 2) * ((nh & 1) ? (1.0 / std::sqrt(2.0)) : 1.0);
         // fixed-point headroom: the max-norm bound (every op's row sum), or
         // for unitary passes the tile 2-norm bound 2^((nh + K) / 2)
@@ -728,17 +795,208 @@ struct PassBuilder {
         return build_phases(q);
     }
 
-    int build_phases(const Pass& p) {
-        // phases (same rule as plan_passes)
-        struct Ph {
-            uint32_t need = 0;
-            int begin = 0, end = 0;
+    // ---- permutations absorbed into exchanges --------------------------
+    // X, CNOT / anti-CNOT (one target, at most one control) and two-target
+    // permutations without controls that are affine on the target bits
+    // (SWAP) map the local index l to an affine function of l: an exchange
+    // writes amplitude l to the slot of that image instead of running a
+    // register op.
+    static int sigma(const PrepOp& P, int s) {   // input sub-index s -> output row
+        for (int r = 0; r < (1 << P.k); ++r)
+            if (P.perm[r] == s) return r;
+        return s;
+    }
+    bool absorbable(const PrepOp& P) const {
+        if (P.kind != KIND_MONO || P.bslot >= 0 || P.k < 1 || P.k > 2) return false;
+        for (int s = 0; s < (1 << P.k); ++s)
+            if (P.v[s] != cplx(1, 0)) return false;
+        for (int j = 0; j < P.k; ++j)
+            if (local_of[P.t[j]] < 0) return false;
+        if (P.k == 1) return popc(P.cmask) <= 1;
+        if (P.cmask != 0) return false;
+        const int s0 = sigma(P, 0);
+        return (sigma(P, 3) ^ s0) == ((sigma(P, 1) ^ s0) ^ (sigma(P, 2) ^ s0));
+    }
+
+    // Affine map of the local index: l -> XOR of col[b] over set bits b of l,
+    // XOR c, XOR w[i].second where the tile's global bit w[i].first is set.
+    struct Affine {
+        uint32_t col[16];
+        uint32_t c = 0;
+        std::vector<std::pair<int, uint32_t>> w;
+        explicit Affine(int K) {
+            for (int b = 0; b < 16; ++b) col[b] = b < K ? (1u << b) : 0u;
+        }
+    };
+
+    // Linear part of an absorbable op applied to a local index vector.
+    uint32_t op_linear(const PrepOp& P, uint32_t u) const {
+        if (P.k == 1) {
+            if (P.cmask == 0) return u;
+            const int lc = local_of[__builtin_ctzll(P.cmask)];
+            if (lc < 0) return u;
+            return u ^ (((u >> lc) & 1u) << local_of[P.t[0]]);
+        }
+        const int l0 = local_of[P.t[0]], l1 = local_of[P.t[1]];   // t[0]: most significant sub-index bit
+        const int s = (int)((((u >> l0) & 1u) << 1) | ((u >> l1) & 1u));
+        const int r = sigma(P, s) ^ sigma(P, 0);
+        u &= ~((1u << l0) | (1u << l1));
+        return u | ((uint32_t)((r >> 1) & 1) << l0) | ((uint32_t)(r & 1) << l1);
+    }
+
+    // f <- op o f
+    void compose(Affine& f, const PrepOp& P) const {
+        for (int b = 0; b < K; ++b) f.col[b] = op_linear(P, f.col[b]);
+        f.c = op_linear(P, f.c);
+        for (auto& t : f.w) t.second = op_linear(P, t.second);
+        if (P.k == 2) {
+            const int s0 = sigma(P, 0);
+            if (s0 & 2) f.c ^= 1u << local_of[P.t[0]];
+            if (s0 & 1) f.c ^= 1u << local_of[P.t[1]];
+            return;
+        }
+        const uint32_t et = 1u << local_of[P.t[0]];
+        if (P.cmask == 0) {
+            f.c ^= et;
+            return;
+        }
+        const int q = __builtin_ctzll(P.cmask);
+        const bool cv = (P.cvals >> q) & 1ull;
+        if (!cv) f.c ^= et;                       // fires when the control bit is 0: 1 ^ bit
+        if (local_of[q] >= 0) return;             // in-tile control: in the linear part
+        for (auto& t : f.w)
+            if (t.first == q) {
+                t.second ^= et;
+                return;
+            }
+        f.w.push_back(std::make_pair(q, et));
+    }
+
+    // ---- shared-memory swizzles ---------------------------------------------
+    // Z maps a local index to its slot: the default XOR-folds the higher bit
+    // groups into the lowest S bits (S = log2 of amplitudes per 128-byte
+    // row) so that strided register gathers hit distinct banks.  An exchange
+    // whose writer permutes the index searches for another Z of the same
+    // form (an invertible map of the low S bits plus a fold of each higher
+    // bit into them) under which the lanes of every 128-byte wavefront of
+    // both the writer and the reader still land in distinct banks.
+    int Sbits() const { return sizeof(V) == 16 ? 3 : 4; }
+    void default_z(uint32_t* z) const {
+        const int S = Sbits();
+        const uint32_t M = (1u << S) - 1u;
+        for (int b = 0; b < 16; ++b) {
+            const uint32_t l = 1u << b;
+            const uint32_t h = l >> S;
+            z[b] = b < K ? (l ^ ((h ^ (h >> S) ^ (h >> (2 * S)) ^ (h >> (3 * S)) ^ (h >> (4 * S))) & M)) : 0u;
+        }
+    }
+    static uint32_t zapply(const uint32_t* z, uint32_t u) {
+        uint32_t r = 0;
+        for (int b = 0; b < 16; ++b)
+            if ((u >> b) & 1u) r ^= z[b];
+        return r;
+    }
+    // S minus the rank of the low-S-bit slot projections of S lane vectors
+    // (0: conflict free; d: 2^d-way conflicts).
+    // (lanes: the first min(S, K - FR) thread-index bits)
+    int nlanes() const { return std::min(Sbits(), K - FR); }
+    int deficiency(const uint32_t* z, const uint32_t* u) const {
+        const int S = Sbits(), m = nlanes();
+        uint32_t rows[8];
+        for (int i = 0; i < m; ++i) rows[i] = zapply(z, u[i]) & ((1u << S) - 1u);
+        return m - rank_of(rows, m, S);
+    }
+    static int rank_of(uint32_t* rows, int m, int S) {
+        int rank = 0;
+        for (int bit = S - 1; bit >= 0; --bit) {
+            int piv = -1;
+            for (int i = rank; i < m; ++i)
+                if ((rows[i] >> bit) & 1u) {
+                    piv = i;
+                    break;
+                }
+            if (piv < 0) continue;
+            std::swap(rows[rank], rows[piv]);
+            for (int i = 0; i < m; ++i)
+                if (i != rank && ((rows[i] >> bit) & 1u)) rows[i] ^= rows[rank];
+            ++rank;
+        }
+        return rank;
+    }
+    void choose_z(uint32_t* z, const uint32_t* wl, const uint32_t* rl, uint32_t seed) const {
+        default_z(z);
+        int best = deficiency(z, wl) + deficiency(z, rl);
+        if (best == 0) return;
+        const int S = Sbits();
+        uint32_t cand[16], keep[16];
+        memcpy(keep, z, sizeof(keep));
+        uint32_t st = 0x9E3779B9u ^ (seed * 0x85EBCA6Bu);
+        auto rnd = [&]() {
+            st ^= st << 13;
+            st ^= st >> 17;
+            st ^= st << 5;
+            return st;
         };
+        for (int trial = 0; trial < 4096 && best > 0; ++trial) {
+            for (int b = 0; b < S; ++b) cand[b] = rnd() & ((1u << S) - 1u);
+            uint32_t low[8];
+            for (int b = 0; b < S; ++b) low[b] = cand[b];
+            if (rank_of(low, S, S) != S) continue;   // the low block must be invertible
+            for (int b = S; b < 16; ++b) cand[b] = b < K ? ((1u << b) | (rnd() & ((1u << S) - 1u))) : 0u;
+            const int d = deficiency(cand, wl) + deficiency(cand, rl);
+            if (d < best) {
+                best = d;
+                memcpy(keep, cand, sizeof(keep));
+            }
+        }
+        memcpy(z, keep, sizeof(keep));
+    }
+    struct Ph {
+        uint32_t need = 0;
+        int begin = 0, end = 0;
+        std::vector<int> exitp;   // permutation ops absorbed at the exit
+    };
+
+    int build_phases(const Pass& p) {
+        const int save_nop = nop, save_ncoef = ncoef, save_nz4 = nz4, save_nnt = nnt;
+        const size_t save_tabs = tabs.size();
+        const OpenTable save_ot = ot;
+        const int r = build_phases_with(p, true);
+        if (r == MERA_OK) return r;
+        // too many phases or exit offsets with absorbed permutations: run
+        // every permutation as a register op
+        nop = save_nop;
+        ncoef = save_ncoef;
+        nz4 = save_nz4;
+        nnt = save_nnt;
+        tabs.resize(save_tabs);
+        ot = save_ot;
+        return build_phases_with(p, false);
+    }
+
+    int build_phases_with(const Pass& p, bool absorb) {
+        // phases: consecutive gates while their targets fit FR register
+        // bits; a run of absorbable permutations ends the phase and becomes
+        // its exit map (runs of one gate only at a phase start or the end)
         std::vector<Ph> phs;
         Ph cur;
-        for (int i = 0; i < (int)p.ops.size(); ++i) {
+        const int nops = (int)p.ops.size();
+        for (int i = 0; i < nops; ++i) {
             const PrepOp& P = ops[p.ops[i]];
             if (P.kind == KIND_DIAG) continue;
+            if (absorb && absorbable(P)) {
+                int j = i;
+                while (j < nops && ops[p.ops[j]].kind != KIND_DIAG && absorbable(ops[p.ops[j]])) ++j;
+                if (j - i >= 2 || cur.need == 0 || j == nops) {
+                    cur.end = i;
+                    for (int m = i; m < j; ++m) cur.exitp.push_back(p.ops[m]);
+                    phs.push_back(cur);
+                    cur = Ph();
+                    cur.begin = j;
+                    i = j - 1;
+                    continue;
+                }
+            }
             uint32_t need = 0;
             for (int t = 0; t < P.k; ++t) need |= 1u << local_of[P.t[t]];
             if (popc(cur.need | need) > FR) {
@@ -751,10 +1009,11 @@ struct PassBuilder {
                 cur.need |= need;
             }
         }
-        cur.end = (int)p.ops.size();
+        cur.end = nops;
         phs.push_back(cur);
         MERA_RETURN_IF((int)phs.size() > TILE_MAX_PHASES, MERA_EUNSUPPORTED, "tile pass with %zu phases", phs.size());
         A.nph = (int)phs.size();
+        std::vector<std::vector<int>> nonreg(A.nph);
         for (int ph = 0; ph < A.nph; ++ph) {
             uint32_t rbm = phs[ph].need;
             for (int b = K - 1; b >= 0 && popc(rbm) < FR; --b)
@@ -766,6 +1025,8 @@ struct PassBuilder {
                 if ((rbm >> b) & 1u) {
                     A.ph[ph].rb[r] = (int8_t)b;
                     reg_of[b] = r++;
+                } else {
+                    nonreg[ph].push_back(b);
                 }
             }
             A.ph[ph].op_begin = (int16_t)nop;
@@ -783,10 +1044,11 @@ struct PassBuilder {
             }
             MERA_TRY(flush_diag(run));
             A.ph[ph].op_end = (int16_t)nop;
+            for (int idx : phs[ph].exitp) note_gate(idx);
         }
         // stage the first load / last store through shared memory unless the
         // lanes cover whole 128-byte rows in global memory
-        const int S = sizeof(V) == 16 ? 3 : 4;
+        const int S = Sbits();
         auto low_reg = [&](int ph) {
             for (int r = 0; r < FR; ++r)
                 if (A.ph[ph].rb[r] < S) return true;
@@ -794,6 +1056,67 @@ struct PassBuilder {
         };
         A.load_smem = low_reg(0) ? 1 : 0;
         A.store_smem = low_reg(A.nph - 1) ? 1 : 0;
+        return build_maps(phs, nonreg);
+    }
+
+    void fill_side(XSide& x, const uint32_t* z, const std::vector<int>& nr, const int8_t* rb,
+                   const Affine* f) const {
+        memset(&x, 0, sizeof(x));
+        auto img = [&](int b) { return zapply(z, f ? f->col[b] : (1u << b)); };
+        for (size_t t = 0; t < nr.size() && t < 12; ++t) x.tc[t] = (int16_t)img(nr[t]);
+        for (int r = 0; r < FR; ++r) x.rc[r] = (int16_t)img(rb[r]);
+    }
+
+    // Slot maps of every exchange: the load staging, the exchanges between
+    // phases (with their absorbed permutations) and the store staging.
+    int build_maps(const std::vector<Ph>& phs, const std::vector<std::vector<int>>& nonreg) {
+        const int np = A.nph;
+        std::vector<int> stage_bits;   // staging copy: lanes on local bits 0..K-FR-1
+        for (int b = 0; b < K - FR; ++b) stage_bits.push_back(b);
+        int8_t stage_rb[FR];
+        for (int r = 0; r < FR; ++r) stage_rb[r] = (int8_t)(K - FR + r);
+        uint32_t zin[16];
+        // load staging -> phase 0
+        {
+            uint32_t wl[8], rl[8];
+            for (int i = 0; i < nlanes(); ++i) {
+                wl[i] = 1u << i;
+                rl[i] = 1u << nonreg[0][i];
+            }
+            choose_z(zin, wl, rl, 1u);
+            fill_side(A.ld, zin, stage_bits, stage_rb, nullptr);
+        }
+        for (int ph = 0; ph < np; ++ph) {
+            TilePhase& T = A.ph[ph];
+            const bool read_sm = ph > 0 || A.load_smem;
+            fill_side(T.in, zin, nonreg[ph], T.rb, nullptr);
+            const bool last = ph == np - 1;
+            if (last && !A.store_smem) {
+                T.permuted = 0;
+                break;
+            }
+            Affine f(K);
+            for (int idx : phs[ph].exitp) compose(f, ops[idx]);
+            MERA_RETURN_IF((int)f.w.size() > TILE_MAX_XOFF, MERA_EUNSUPPORTED, "exchange with %zu tile-dependent offsets",
+                           f.w.size());
+            uint32_t zout[16], wl[8], rl[8];
+            for (int i = 0; i < nlanes(); ++i) {
+                wl[i] = f.col[nonreg[ph][i]];
+                rl[i] = last ? (1u << i) : (1u << nonreg[ph + 1][i]);
+            }
+            choose_z(zout, wl, rl, 2u + (uint32_t)ph);
+            fill_side(T.out.s, zout, nonreg[ph], T.rb, &f);
+            T.out.off0 = (int16_t)zapply(zout, f.c);
+            T.out.noff = (int8_t)f.w.size();
+            for (size_t i = 0; i < f.w.size(); ++i) {
+                T.out.offq[i] = (int8_t)f.w[i].first;
+                T.out.offv[i] = (int16_t)zapply(zout, f.w[i].second);
+            }
+            const bool same = memcmp(&T.out.s, &T.in, sizeof(XSide)) == 0 && T.out.off0 == 0 && T.out.noff == 0;
+            T.permuted = (!read_sm || !same) ? 1 : 0;
+            if (last) fill_side(A.st, zout, stage_bits, stage_rb, nullptr);
+            memcpy(zin, zout, sizeof(zin));
+        }
         return MERA_OK;
     }
 };
@@ -864,7 +1187,7 @@ int launch_tile<float2>(int, int, dim3 grid, unsigned block, size_t smem, cudaSt
 // engine and kernel variant per pass, and the diagonal tables.  Passes with
 // `single` >= 0 are per-gate ops (returned in `singles`, -1 otherwise).
 template <typename V>
-int fused_build(int n, const std::vector<PrepOp>& ops, FusedPlan<V>& plan) {
+int fused_build(int n, const std::vector<PrepOp>& ops, FusedPlan<V>& plan, bool fp_only) {
     plan.K = fused_tile_bits(sizeof(V) == 16 ? MERA_C128 : MERA_C64, n);
     plan.n = n;
     const int L = low_bits_for(sizeof(V) == 16 ? MERA_C128 : MERA_C64, plan.K);
@@ -882,6 +1205,7 @@ int fused_build(int n, const std::vector<PrepOp>& ops, FusedPlan<V>& plan) {
             continue;
         }
         PassBuilder<V> b(plan.args[i], plan.tabs, ops, plan.K, n);
+        b.fp_only = fp_only;
         MERA_TRY(b.build(passes[i], sizeof(V) == 16));
         plan.eng[i] = b.i64 ? 1 : 0;
         plan.feat[i] = (unsigned char)round_feat(plan.eng[i], b.features(), sizeof(V) == 16);
@@ -903,15 +1227,27 @@ int fused_launch(const FusedPlan<V>& plan, size_t i, PassArgs<V>& A, unsigned ny
     return launch_end(st);
 }
 
-template int fused_build<double2>(int, const std::vector<PrepOp>&, FusedPlan<double2>&);
-template int fused_build<float2>(int, const std::vector<PrepOp>&, FusedPlan<float2>&);
+template int fused_build<double2>(int, const std::vector<PrepOp>&, FusedPlan<double2>&, bool);
+template int fused_build<float2>(int, const std::vector<PrepOp>&, FusedPlan<float2>&, bool);
 template int fused_launch<double2>(const FusedPlan<double2>&, size_t, PassArgs<double2>&, unsigned, cudaStream_t);
 template int fused_launch<float2>(const FusedPlan<float2>&, size_t, PassArgs<float2>&, unsigned, cudaStream_t);
 
+struct FusedCache {
+    std::vector<unsigned char> key;
+    std::vector<PrepOp> ops;
+    FusedPlan<double2> p128;
+    FusedPlan<float2> p64;
+};
+
+void fused_cache_free(mera_state* s) {
+    delete reinterpret_cast<FusedCache*>(s->fused_cache);
+    s->fused_cache = nullptr;
+}
+
+// Upload a plan's diagonal tables into the state's program buffer (grown on
+// demand) and point every pass at the state and the tables.
 template <typename V>
-static int run_fused(mera_state* s, const std::vector<PrepOp>& ops) {
-    FusedPlan<V> plan;
-    MERA_TRY(fused_build<V>(s->n, ops, plan));
+static int upload_plan(mera_state* s, FusedPlan<V>& plan) {
     const V* dtab = nullptr;
     if (!plan.tabs.empty()) {
         const size_t bytes = plan.tabs.size() * sizeof(V);
@@ -931,17 +1267,91 @@ static int run_fused(mera_state* s, const std::vector<PrepOp>& ops) {
         MERA_CHECK_CUDA(cudaMemcpyAsync(s->prog, plan.tabs.data(), bytes, cudaMemcpyHostToDevice, s->stream));
         dtab = reinterpret_cast<const V*>(s->prog);
     }
+    for (PassArgs<V>& A : plan.args) {
+        A.psi = reinterpret_cast<V*>(s->data);
+        A.tab = dtab;
+    }
+    return MERA_OK;
+}
+
+template <typename V>
+static int launch_plan(mera_state* s, FusedPlan<V>& plan, const std::vector<PrepOp>& ops) {
     for (size_t i = 0; i < plan.args.size(); ++i) {
         if (plan.single[i] >= 0) {
             MERA_TRY(apply_prepared(s, ops[plan.single[i]]));
             continue;
         }
-        PassArgs<V>& A = plan.args[i];
-        A.psi = reinterpret_cast<V*>(s->data);
-        A.tab = dtab;
-        MERA_TRY(fused_launch<V>(plan, i, A, 1, s->stream));
+        plan.args[i].psi = reinterpret_cast<V*>(s->data);
+        MERA_TRY(fused_launch<V>(plan, i, plan.args[i], 1, s->stream));
     }
     return MERA_OK;
+}
+
+template <typename V>
+static int run_fused(mera_state* s, const std::vector<PrepOp>& ops) {
+    fused_cache_free(s);   // the program buffer is about to hold other tables
+    FusedPlan<V> plan;
+    MERA_TRY(fused_build<V>(s->n, ops, plan));
+    MERA_TRY(upload_plan<V>(s, plan));
+    return launch_plan<V>(s, plan, ops);
+}
+
+// The key of a circuit: qubit count, dtype, tile geometry and every op's
+// bytes (explicit matrices by value).
+static std::vector<unsigned char> circuit_key(const mera_state* s, const mera_op* ops, size_t nops) {
+    std::vector<unsigned char> k;
+    const int K = fused_tile_bits(s->dtype, s->n);
+    const int head[4] = {s->n, s->dtype, K, low_bits_for(s->dtype, K)};
+    k.insert(k.end(), (const unsigned char*)head, (const unsigned char*)(head + 4));
+    for (size_t j = 0; j < nops; ++j) {
+        mera_op o = ops[j];
+        const double* m = o.matrix;
+        o.matrix = nullptr;
+        k.insert(k.end(), (const unsigned char*)&o, (const unsigned char*)(&o + 1));
+        if (o.gate == MERA_GATE_MATRIX && m && o.nt >= 0 && o.nt <= 3) {
+            const size_t d = (size_t)1 << o.nt;
+            k.insert(k.end(), (const unsigned char*)m, (const unsigned char*)(m + 2 * d * d));
+        }
+    }
+    return k;
+}
+
+int apply_fused_circuit(mera_state* s, const mera_op* ops, size_t nops) {
+    FusedCache* c = reinterpret_cast<FusedCache*>(s->fused_cache);
+    std::vector<unsigned char> key = circuit_key(s, ops, nops);
+    if (c && c->key == key) {
+        if (s->dtype == MERA_C128) return launch_plan<double2>(s, c->p128, c->ops);
+        return launch_plan<float2>(s, c->p64, c->ops);
+    }
+    std::vector<PrepOp> prep(nops);
+    for (size_t j = 0; j < nops; ++j) {
+        int st = prepare_op(ops[j], s->n, &prep[j]);
+        if (st != MERA_OK) {
+            std::string msg = last_error();
+            set_error("op %zu: %s", j, msg.c_str());
+            return st;
+        }
+    }
+    if (s->n < FR + 1) return apply_fused(s, prep);
+    fused_cache_free(s);
+    c = new FusedCache();
+    c->ops.swap(prep);
+    int st;
+    if (s->dtype == MERA_C128) {
+        st = fused_build<double2>(s->n, c->ops, c->p128);
+        if (st == MERA_OK) st = upload_plan<double2>(s, c->p128);
+    } else {
+        st = fused_build<float2>(s->n, c->ops, c->p64);
+        if (st == MERA_OK) st = upload_plan<float2>(s, c->p64);
+    }
+    if (st != MERA_OK) {
+        delete c;
+        return st;
+    }
+    c->key.swap(key);
+    s->fused_cache = c;
+    if (s->dtype == MERA_C128) return launch_plan<double2>(s, c->p128, c->ops);
+    return launch_plan<float2>(s, c->p64, c->ops);
 }
 
 // Host-only description of the plan (no device work).
@@ -968,11 +1378,18 @@ static int describe_fused(int n, int dtype, const std::vector<PrepOp>& ops, std:
         for (int o = 0; o < b.nop; ++o) cnt[A.ops[o].type]++;
         std::string bits;
         for (int j = 0; j < K; ++j) bits += std::to_string(A.tpos[j]) + (j + 1 < K ? "," : "");
+        std::string dsep;
+        for (int o = 0; o < b.nop; ++o)
+            if (A.ops[o].type == TOP_DSEP) dsep += " dsep_nontile=" + std::to_string((int)A.ops[o].nt);
+        dsep += " phase_ops=[";
+        for (int ph = 0; ph < A.nph; ++ph)
+            dsep += std::to_string(A.ph[ph].op_end - A.ph[ph].op_begin) + (A.ph[ph].permuted ? "p" : "") +
+                    (ph + 1 < A.nph ? "," : "]");
         snprintf(line, sizeof(line),
                  "pass %zu: eng=%s nh=%d phases=%d ops=%d [g1=%d mono=%d h=%d g2=%d diag=%d dsep=%d z4=%d] "
-                 "guard=%d load_smem=%d store_smem=%d tile={%s}\n",
+                 "guard=%d load_smem=%d store_smem=%d tile={%s}%s\n",
                  i, b.i64 ? "i64" : "fp", A.nh, A.nph, b.nop, cnt[TOP_G1], cnt[TOP_G1MONO] + cnt[TOP_G2MONO] + cnt[TOP_G1SWAP], cnt[TOP_H],
-                 cnt[TOP_G2], cnt[TOP_DIAG], cnt[TOP_DSEP], cnt[TOP_Z4], A.guard, A.load_smem, A.store_smem, bits.c_str());
+                 cnt[TOP_G2], cnt[TOP_DIAG], cnt[TOP_DSEP], cnt[TOP_Z4], A.guard, A.load_smem, A.store_smem, bits.c_str(), dsep.c_str());
         *out += line;
     }
     if (npasses) *npasses = (int)passes.size();

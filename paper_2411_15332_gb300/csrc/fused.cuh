@@ -18,8 +18,9 @@ struct FusedPlan {
     std::vector<V> tabs;                  // diagonal tables to upload (PassArgs::tab)
 };
 
+// fp_only: every pass in the float engine (coefficients as plain values).
 template <typename V>
-int fused_build(int n, const std::vector<PrepOp>& ops, FusedPlan<V>& plan);
+int fused_build(int n, const std::vector<PrepOp>& ops, FusedPlan<V>& plan, bool fp_only = false);
 template <typename V>
 int fused_launch(const FusedPlan<V>& plan, size_t i, PassArgs<V>& A, unsigned ny, cudaStream_t st);
 

@@ -73,11 +73,32 @@ __device__ __forceinline__ I2 neg_v(I2 x) {
 
 // Multiply by a phase given as a code: 0 -> 1, 1 -> i, 2 -> -1, 3 -> -i
 // (exact: only moves and sign flips), 4 -> the general value v.
-// Sign flips as integer operations on the sign bit (no FP64 instruction).
-__device__ __forceinline__ double dneg(double v) {
-    return __hiloint2double(__double2hiint(v) ^ (int)0x80000000, __double2loint(v));
+// Sign flips as integer operations on the sign bit.  The XOR is inline PTX
+// so that the compiler cannot turn it back into a floating-point negation
+// (which would occupy the FP64 pipe, ~57x scarcer than the integer ALUs).
+__device__ __forceinline__ int xor_sign(int h) {
+    int r;
+    asm("xor.b32 %0, %1, 0x80000000;" : "=r"(r) : "r"(h));
+    return r;
 }
-__device__ __forceinline__ float fneg(float v) { return __int_as_float(__float_as_int(v) ^ (int)0x80000000); }
+__device__ __forceinline__ double dneg(double v) {
+    return __hiloint2double(xor_sign(__double2hiint(v)), __double2loint(v));
+}
+__device__ __forceinline__ float fneg(float v) { return __int_as_float(xor_sign(__float_as_int(v))); }
+// v with its sign bit XORed with bit 31 of m (m is 0 or 0x80000000)
+__device__ __forceinline__ int xor_reg(int h, int m) {
+    int r;
+    asm("xor.b32 %0, %1, %2;" : "=r"(r) : "r"(h), "r"(m));
+    return r;
+}
+__device__ __forceinline__ double flip_sign(double v, int m) {
+    return __hiloint2double(xor_reg(__double2hiint(v), m), __double2loint(v));
+}
+__device__ __forceinline__ float flip_sign(float v, int m) { return __int_as_float(xor_reg(__float_as_int(v), m)); }
+__device__ __forceinline__ long long flip_sign(long long v, int m) {
+    const long long s = (long long)(m >> 31);   // 0 or -1 (arithmetic shift)
+    return (v ^ s) - s;
+}
 __device__ __forceinline__ double sneg(double v) { return dneg(v); }
 __device__ __forceinline__ float sneg(float v) { return fneg(v); }
 __device__ __forceinline__ double2 neg_v(double2 x) { return make_double2(dneg(x.x), dneg(x.y)); }

@@ -115,6 +115,18 @@ static V mk(double re, double im) {
     return r;
 }
 
+// A coefficient for the tile passes: plain values, or Q62 fixed point
+// (value * 2^62 as int64 in the same 16 bytes) for the int64 engine.
+template <typename V>
+static V mkq(double re, double im, bool q62) {
+    if (!q62 || sizeof(V) != 16) return mk<V>(re, im);
+    const double sc = 4611686018427387904.0;   // 2^62
+    const long long q[2] = {std::llround(re * sc), std::llround(im * sc)};
+    V r;
+    memcpy(&r, q, sizeof(r));
+    return r;
+}
+
 // ---------------------------------------------------------------- kernels --
 template <typename V>
 __global__ void k_batch_zero(V* states, const int* slots, uint64_t N) {
@@ -318,6 +330,14 @@ static int batch_layer_t(mera_batch* b, const int* slots, int nslots, const doub
         std::vector<PrepOp> ops;
         int st = layer_ops(n, ops);
         if (st == MERA_OK) st = fused_build<V>(n, ops, *plan);
+        // one coefficient encoding serves every pass: a plan that mixes the
+        // int64 and float engines is rebuilt in the float engine
+        bool mixed = false;
+        for (size_t i = 1; st == MERA_OK && i < plan->eng.size(); ++i) mixed = mixed || plan->eng[i] != plan->eng[0];
+        if (st == MERA_OK && mixed) {
+            *plan = FusedPlan<V>();
+            st = fused_build<V>(n, ops, *plan, true);
+        }
         if (st != MERA_OK) {
             delete plan;
             return st;
@@ -325,6 +345,7 @@ static int batch_layer_t(mera_batch* b, const int* slots, int nslots, const doub
         MERA_RETURN_IF(!plan->tabs.empty(), MERA_EUNSUPPORTED, "unexpected diagonal tables in the layer plan");
         b->layer_plan = plan;
     }
+    const bool q62 = !plan->eng.empty() && plan->eng[0] == 1;
     // per-row coefficients: RZ(b) RY(a) for every qubit
     std::vector<V> cf((size_t)nslots * n * 4);
     for (int r = 0; r < nslots; ++r)
@@ -334,10 +355,10 @@ static int batch_layer_t(mera_batch* b, const int* slots, int nslots, const doub
             const double c = std::cos(a / 2), s = std::sin(a / 2);
             const double er = std::cos(bb / 2), ei = std::sin(bb / 2);   // e^{ib/2}
             V* m = &cf[((size_t)r * n + q) * 4];
-            m[0] = mk<V>(er * c, -ei * c);      // e^{-ib/2} c
-            m[1] = mk<V>(-er * s, ei * s);      // -e^{-ib/2} s
-            m[2] = mk<V>(er * s, ei * s);       // e^{ib/2} s
-            m[3] = mk<V>(er * c, ei * c);       // e^{ib/2} c
+            m[0] = mkq<V>(er * c, -ei * c, q62);      // e^{-ib/2} c
+            m[1] = mkq<V>(-er * s, ei * s, q62);      // -e^{-ib/2} s
+            m[2] = mkq<V>(er * s, ei * s, q62);       // e^{ib/2} s
+            m[3] = mkq<V>(er * c, ei * c, q62);       // e^{ib/2} c
         }
     MERA_TRY(grow(&b->coef, &b->coef_bytes, cf.size() * sizeof(V)));
     MERA_CHECK_CUDA(cudaMemcpyAsync(b->coef, cf.data(), cf.size() * sizeof(V), cudaMemcpyHostToDevice, b->stream));

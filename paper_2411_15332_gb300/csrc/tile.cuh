@@ -81,9 +81,33 @@ struct Z4Term {
     int32_t pad;
 };
 
+// Shared-memory slot map of one side of an exchange: the slot of a
+// thread's register slot j is the XOR of tc[t] over the set bits t of the
+// thread index and of rc[r] over the set bits r of j.  The maps are linear
+// over GF(2): a swizzle Z (bank spreading) composed, on the writing side,
+// with the affine index permutation the exchange applies.
+constexpr int TILE_MAX_XOFF = 6;
+struct XSide {
+    int16_t tc[12];
+    int16_t rc[FR];
+};
+
+// Writing side of an exchange: the slot map plus a block-dependent offset
+// (XOR of offv[i] where the tile's bit at global position offq[i] is set).
+struct XOut {
+    XSide s;
+    int16_t off0;
+    int8_t noff;
+    int8_t offq[TILE_MAX_XOFF];
+    int16_t offv[TILE_MAX_XOFF];
+};
+
 struct TilePhase {
     int8_t rb[FR];       // local tile bits held in registers, ascending
     int16_t op_begin, op_end;
+    int8_t permuted;     // 1: the exit map differs from the entry map (all reads finish first)
+    XSide in;            // slots this phase reads (from the previous exchange or the load staging)
+    XOut out;            // slots this phase writes (next exchange or the store staging)
 };
 
 template <typename V>
@@ -105,6 +129,8 @@ struct PassArgs {
     int nh;              // Hadamard butterflies in the pass (ENG_I64 scales by 2^-nh/2)
     int guard;           // ENG_I64: headroom bits of the fixed-point format
     int tpos[16];        // global bit of local bit j, ascending
+    XSide ld;            // load staging: slot of element tid + i * 2^(K-FR)
+    XSide st;            // store staging: the same for the final copy out
     int8_t ntq[TILE_MAX_NT];   // global positions of separable non-tile factors
     TilePhase ph[TILE_MAX_PHASES];
     TileOp ops[TILE_MAX_OPS];
@@ -122,17 +148,6 @@ struct IsFP<I2> {
 };
 
 // ----------------------------------------------------------- bit helpers --
-// Shared-memory slot of local index l: XOR-fold the higher bit groups into
-// the lowest S bits (S = log2 of amplitudes per 128-byte row) so that the
-// strided register gathers hit distinct banks.
-template <int EB>
-__device__ __forceinline__ int swz(int l) {
-    constexpr int S = EB == 16 ? 3 : 4;
-    constexpr int M = (1 << S) - 1;
-    const int h = l >> S;
-    return l ^ ((h ^ (h >> S) ^ (h >> (2 * S)) ^ (h >> (3 * S)) ^ (h >> (4 * S))) & M);
-}
-
 // Deposit the bits of local index l at the global positions tpos[].
 __device__ __forceinline__ uint64_t spread_bits(uint32_t l, const int* tpos, int K) {
     uint64_t g = 0;
@@ -176,6 +191,21 @@ __device__ __forceinline__ int dep4x(int j, const int* m) {
     return r;
 }
 
+// Slot base of a thread on one side of an exchange.
+__device__ __forceinline__ int xbase(const XSide& s, uint32_t tid) {
+    int v = 0;
+#pragma unroll
+    for (int t = 0; t < 12; ++t) v ^= (-(int)((tid >> t) & 1u)) & (int)s.tc[t];
+    return v;
+}
+
+__device__ __forceinline__ int xbase_out(const XOut& o, uint32_t tid, uint64_t gb) {
+    int v = xbase(o.s, tid) ^ (int)o.off0;
+    for (int i = 0; i < o.noff; ++i)
+        if ((gb >> o.offq[i]) & 1ull) v ^= (int)o.offv[i];
+    return v;
+}
+
 // 16-bit mask of this thread's register slots whose controls hold: the
 // non-register control bits are fixed for the thread, the register ones
 // select slots.
@@ -199,8 +229,10 @@ __device__ __forceinline__ V mul_ik(V x, int k) {
         r.x = x.y;
         r.y = x.x;
     }
-    if (k == 1 || k == 2) r.x = sneg(r.x);
-    if (k >= 2) r.y = sneg(r.y);
+    // sign masks: re negated for k = 1, 2; im for k = 2, 3
+    const int mx = (int)((unsigned)(((k + 1) >> 1) & 1) << 31), my = (int)((unsigned)((k >> 1) & 1) << 31);
+    r.x = flip_sign(r.x, mx);
+    r.y = flip_sign(r.y, my);
     return r;
 }
 
@@ -234,6 +266,71 @@ __device__ __forceinline__ I2 tab_ld(const I2* p) {
     r.x = v.x;
     r.y = v.y;
     return r;
+}
+
+// ------------------------------------------- int64 block floating point --
+// Biased exponent field of a double (0 for zero / subnormal).
+__device__ __forceinline__ int dexp(double v) {
+    return (int)((__double_as_longlong(v) >> 52) & 0x7FF);
+}
+
+// round(v * 2^S) as int64, for |v| * 2^S < 2^62 (subnormals read as 0).
+__device__ __forceinline__ long long d2fix(double v, int S) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)((b >> 52) & 0x7FF);
+    if (e == 0) return 0;
+    const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = S + e - 1075;
+    unsigned long long a;
+    if (sh >= 0) a = m << sh;
+    else if (sh > -64) a = (m + (1ull << (-sh - 1))) >> (-sh);
+    else a = 0;
+    return (b >> 63) ? -(long long)a : (long long)a;
+}
+
+// v * 2^-S rounded to nearest even (values below the normal range flush to 0).
+__device__ __forceinline__ double fix2d(long long v, int S) {
+    if (v == 0) return 0.0;
+    const unsigned long long sgn = v < 0 ? (1ull << 63) : 0ull;
+    const unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+    int lz = __clzll((long long)a);
+    const unsigned long long m = a << lz;
+    unsigned long long r = m >> 11;
+    const unsigned long long rem = m & 0x7FFull;
+    if (rem > 0x400ull || (rem == 0x400ull && (r & 1ull))) {
+        r += 1;
+        if (r >> 53) {
+            r >>= 1;
+            lz -= 1;
+        }
+    }
+    const int e = (63 - lz) - S + 1023;
+    if (e <= 0) return __longlong_as_double((long long)sgn);
+    return __longlong_as_double((long long)(sgn | ((unsigned long long)e << 52) | (r & 0xFFFFFFFFFFFFFull)));
+}
+
+
+// x * d for a complex128 amplitude held as doubles and a Q62 table entry d
+// (|d| <= 1) without FP64 instructions: both parts of x are aligned to the
+// larger of their exponents as 62-bit integers, multiplied with full
+// 128-bit products (Q62) and rounded back to double (nearest even).  Zero
+// and subnormal parts read as 0.  Error: about one unit in the last place
+// of max(|Re x|, |Im x|).
+__device__ __forceinline__ long long align62(long long b, int eb, int e) {
+    if (eb == 0 || e - eb > 61) return 0;
+    const long long m = (long long)((((unsigned long long)b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 9) >> (e - eb);
+    return b < 0 ? -m : m;
+}
+__device__ __forceinline__ double2 icmul(I2 d, double2 x) {
+    const long long br = __double_as_longlong(x.x), bi = __double_as_longlong(x.y);
+    const int er = (int)((br >> 52) & 0x7FF), ei = (int)((bi >> 52) & 0x7FF);
+    const int e = max(er, ei);
+    if (e == 0) return make_double2(0.0, 0.0);
+    const long long xr = align62(br, er, e), xi = align62(bi, ei, e);
+    const long long pr = mulq62(d.x, xr) - mulq62(d.y, xi);
+    const long long pi = mulq62(d.x, xi) + mulq62(d.y, xr);
+    const int S = 1084 - e;   // the products carry the scale 2^(e - 1075 - 9)
+    return make_double2(fix2d(pr, S), fix2d(pi, S));
 }
 
 // ------------------------------------------------------------ op bodies --
@@ -379,20 +476,42 @@ __device__ __forceinline__ void op_dsep(V (&x)[FRA], const TileOp& o, const V* c
     const int nsel = o.nt < DSEP_SEL_BITS ? o.nt : DSEP_SEL_BITS;
     uint32_t sel = 0;
     for (int f = 0; f < nsel; ++f) sel |= (uint32_t)((gb >> ntq[o.aux2 + f]) & 1ull) << f;
-    const V* t = tab + o.aux + ((size_t)sel << K);
-    bool have_c = false;
-    V c = cf[0];
-    for (int f = nsel; f < o.nt; ++f) {
-        if ((gb >> ntq[o.aux2 + f]) & 1ull) {
-            c = have_c ? cmul(c, cf[f - nsel]) : cf[f - nsel];
-            have_c = true;
+    if constexpr (std::is_same<V, double2>::value) {
+        // complex128 in the float engine: Q62 tables and factors, integer
+        // multiplies (no FP64 instruction)
+        const I2* t = reinterpret_cast<const I2*>(tab) + o.aux + ((size_t)sel << K);
+        const I2* cq = reinterpret_cast<const I2*>(cf);
+        bool have_c = false;
+        I2 c = cq[0];
+        for (int f = nsel; f < o.nt; ++f) {
+            if ((gb >> ntq[o.aux2 + f]) & 1ull) {
+                c = have_c ? cmul(c, cq[f - nsel]) : cq[f - nsel];
+                have_c = true;
+            }
         }
-    }
+        if (have_c) {
 #pragma unroll
-    for (int j = 0; j < FRA; ++j) {
-        V d = tab_ld(t + (lb | dep4(j, lm)));
-        if (have_c) d = cmul(c, d);
-        x[j] = cmul(d, x[j]);
+            for (int j = 0; j < FRA; ++j) x[j] = icmul(cmul(c, tab_ld(t + (lb | dep4(j, lm)))), x[j]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < FRA; ++j) x[j] = icmul(tab_ld(t + (lb | dep4(j, lm))), x[j]);
+        }
+    } else {
+        const V* t = tab + o.aux + ((size_t)sel << K);
+        bool have_c = false;
+        V c = cf[0];
+        for (int f = nsel; f < o.nt; ++f) {
+            if ((gb >> ntq[o.aux2 + f]) & 1ull) {
+                c = have_c ? cmul(c, cf[f - nsel]) : cf[f - nsel];
+                have_c = true;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < FRA; ++j) {
+            V d = tab_ld(t + (lb | dep4(j, lm)));
+            if (have_c) d = cmul(c, d);
+            x[j] = cmul(d, x[j]);
+        }
     }
 }
 
@@ -456,47 +575,6 @@ __device__ __forceinline__ void apply_tile_op(V (&x)[FRA], const TileOp& o, cons
     }
 }
 
-// ------------------------------------------- int64 block floating point --
-// Biased exponent field of a double (0 for zero / subnormal).
-__device__ __forceinline__ int dexp(double v) {
-    return (int)((__double_as_longlong(v) >> 52) & 0x7FF);
-}
-
-// round(v * 2^S) as int64, for |v| * 2^S < 2^62 (subnormals read as 0).
-__device__ __forceinline__ long long d2fix(double v, int S) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-    const int e = (int)((b >> 52) & 0x7FF);
-    if (e == 0) return 0;
-    const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    const int sh = S + e - 1075;
-    unsigned long long a;
-    if (sh >= 0) a = m << sh;
-    else if (sh > -64) a = (m + (1ull << (-sh - 1))) >> (-sh);
-    else a = 0;
-    return (b >> 63) ? -(long long)a : (long long)a;
-}
-
-// v * 2^-S rounded to nearest even (values below the normal range flush to 0).
-__device__ __forceinline__ double fix2d(long long v, int S) {
-    if (v == 0) return 0.0;
-    const unsigned long long sgn = v < 0 ? (1ull << 63) : 0ull;
-    const unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
-    int lz = __clzll((long long)a);
-    const unsigned long long m = a << lz;
-    unsigned long long r = m >> 11;
-    const unsigned long long rem = m & 0x7FFull;
-    if (rem > 0x400ull || (rem == 0x400ull && (r & 1ull))) {
-        r += 1;
-        if (r >> 53) {
-            r >>= 1;
-            lz -= 1;
-        }
-    }
-    const int e = (63 - lz) - S + 1023;
-    if (e <= 0) return __longlong_as_double((long long)sgn);
-    return __longlong_as_double((long long)(sgn | ((unsigned long long)e << 52) | (r & 0xFFFFFFFFFFFFFull)));
-}
-
 // ---------------------------------------------------------------- kernel --
 // Raw bits of a stored value, held in the int64 engine's registers until the
 // tile exponent is known.
@@ -544,8 +622,8 @@ __global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
         for (int r = 0; r < FR; ++r) gtop[r] = 1ull << a.tpos[K - FR + r];
         int st[FR];
 #pragma unroll
-        for (int r = 0; r < FR; ++r) st[r] = swz<EB>((int)(T << r));
-        const int s0 = swz<EB>((int)tid);
+        for (int r = 0; r < FR; ++r) st[r] = a.ld.rc[r];
+        const int s0 = xbase(a.ld, tid);
 #pragma unroll
         for (int i = 0; i < FRA; ++i) sms[s0 ^ dep4x(i, st)] = __ldcs(psi + (gt | dep4(i, gtop)));
         __syncthreads();
@@ -561,9 +639,10 @@ __global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
         for (int r = 0; r < FR; ++r) {
             gm[r] = 1ull << a.tpos[ph.rb[r]];
             lm[r] = 1 << ph.rb[r];
-            sr[r] = swz<EB>(lm[r]);
+            sr[r] = ph.in.rc[r];
         }
-        const int sb = swz<EB>((int)lb);   // swizzle is XOR-linear: slot = sb ^ xor of sr
+        const bool read_sm = p > 0 || a.load_smem;
+        const int sb = read_sm ? xbase(ph.in, tid) : 0;   // slot maps are XOR-linear: slot = sb ^ xor of sr
         if (p == 0) {
             if (!a.load_smem) {
 #pragma unroll
@@ -601,10 +680,22 @@ __global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
             const V* cf = (op.c ? bcf : reinterpret_cast<const V*>(a.coef)) + op.coef;
             apply_tile_op<V, SV, FEAT>(x, op, a, cf, gb, gm, lb, lm);
         }
-        if (p != a.nph - 1) {
-            // each slot is read and written by its owner only within a phase
+        // exit slots: the same as the entry slots unless the exchange
+        // permutes the tile index, in which case every read of this phase
+        // must finish before any write
+        int ob = sb, orr[FR];
+        if (ph.permuted) {
+            if (read_sm) __syncthreads();
+            ob = xbase_out(ph.out, tid, gb);
 #pragma unroll
-            for (int j = 0; j < FRA; ++j) sm[sb ^ dep4x(j, sr)] = x[j];
+            for (int r = 0; r < FR; ++r) orr[r] = ph.out.s.rc[r];
+        } else {
+#pragma unroll
+            for (int r = 0; r < FR; ++r) orr[r] = sr[r];
+        }
+        if (p != a.nph - 1) {
+#pragma unroll
+            for (int j = 0; j < FRA; ++j) sm[ob ^ dep4x(j, orr)] = x[j];
             __syncthreads();
             continue;
         }
@@ -638,9 +729,9 @@ __global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
 #pragma unroll
             for (int j = 0; j < FRA; ++j) __stcs(psi + (gb | dep4(j, gm)), out[j]);
         } else {
-            // a thread rewrites only the slots it read itself in this phase
+            // unpermuted: a thread rewrites only the slots it read itself
 #pragma unroll
-            for (int j = 0; j < FRA; ++j) sms[sb ^ dep4x(j, sr)] = out[j];
+            for (int j = 0; j < FRA; ++j) sms[ob ^ dep4x(j, orr)] = out[j];
             __syncthreads();
             const uint64_t gt = tb | spread_bits(tid, a.tpos, K - FR);
             uint64_t gtop[FR];
@@ -648,8 +739,8 @@ __global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
             for (int r = 0; r < FR; ++r) gtop[r] = 1ull << a.tpos[K - FR + r];
             int st[FR];
 #pragma unroll
-            for (int r = 0; r < FR; ++r) st[r] = swz<EB>((int)(T << r));
-            const int s0 = swz<EB>((int)tid);
+            for (int r = 0; r < FR; ++r) st[r] = a.st.rc[r];
+            const int s0 = xbase(a.st, tid);
 #pragma unroll
             for (int i = 0; i < FRA; ++i) __stcs(psi + (gt | dep4(i, gtop)), sms[s0 ^ dep4x(i, st)]);
         }
