@@ -287,6 +287,24 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def _arith_dtype(args):
+    """What the timed kernels compute in: complex128 fused passes keep the
+    state as int64 fixed point; the per-gate kernels use float64."""
+    if args.dtype == "c64":
+        return "f32"
+    return "i64" if args.mode == "fused" else "f64"
+
+
+def _arith_note(args):
+    if args.dtype == "c64":
+        return "float32 state and arithmetic, float64 reductions"
+    if args.mode == "fused":
+        return ("complex128 state held as int64 fixed point across the circuit's tile passes "
+                "(global scale from a norm bound; exact butterflies and moves; 31-bit-limb integer "
+                "products for phases, unbiased rounding); float64 at the circuit's ends and in reductions")
+    return "float64 per-gate kernels"
+
+
 def run_mera(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -346,7 +364,7 @@ def run_mera(args, rank, world, local_rank):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None,
                 "traffic": tr["dram_bytes_per_launch"] if tr else None,
-                "kernel": "k_tile<double2>" if kcls == "tile" else "per-gate kernels",
+                "kernel": "k_tile (fused tile passes)" if kcls == "tile" else "per-gate kernels",
                 "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                 "kernel_launches": nl, "kernel_ms": kms,
                 "kernel_share": kms / total_ms if total_ms else None,
@@ -395,9 +413,10 @@ def run_mera(args, rank, world, local_rank):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.dtype == "c128" else "f32",
+                "scaling": "weak", "vs_baseline": None, "dtype": _arith_dtype(args),
                 "data": "synthetic",
-                "config": {"workload": _workload_name(args), "n": n,
+                "config": {"workload": _workload_name(args), "n": n, "state": "complex128" if args.dtype == "c128" else "complex64",
+                           "arithmetic": _arith_note(args),
                            "amplitude_updates_per_step": upd, "mode": args.mode,
                            "parallelism": f"replicas x{world}",
                            "l2": "state (%d GiB) larger than L2 (129 MB); no flush needed" % (((1 << n) * (16 if args.dtype == 'c128' else 8)) >> 30),

@@ -83,6 +83,9 @@ static bool op_is_exact(const PrepOp& P) {
 // Passes with at least this many Hadamard levels take exact gates only;
 // other gates wait for the next pass.
 static constexpr int H_HEAVY = 3;
+// At most this many Hadamard levels per pass (growth 2^(H_MAX_PASS / 2)
+// before the pass scale).
+static constexpr int H_MAX_PASS = 16;
 
 static int coef_need(const PrepOp& P) {
     if (P.bslot >= 0) return 0;
@@ -203,6 +206,9 @@ static void plan_segment(const std::vector<PrepOp>& ops, std::vector<int> remain
             // Hadamard-heavy passes keep to exact gates (butterflies, moves,
             // unit phases): their kernel variant stays lean
             if (take && !op_is_exact(P) && nh >= H_HEAVY) take = false;
+            // the pass scale 2^(-nh/2) applies at its end: cap the growth of
+            // the unnormalised butterflies (fixed-point headroom)
+            if (take && P.is_h && nh >= H_MAX_PASS) take = false;
             if (take && (nops + 1 > TILE_MAX_OPS || ncoef + coef_need(P) > TILE_MAX_COEF)) take = false;
             if (take && P.kind != KIND_DIAG) {
                 const uint64_t t = op_targets(P);
@@ -312,8 +318,10 @@ struct PassBuilder {
     int K, n;
     int local_of[64];
     int nop = 0, ncoef = 0, nz4 = 0, nnt = 0;
-    bool i64 = false;
+    bool i64 = false;       // coefficients in Q62 fixed point (int64 engines)
+    int engine = ENG_FP;
     bool fp_only = false;   // keep every pass in the float engine
+    bool qres = false;      // resident fixed point: every pass in ENG_Q
 
     // The open separable-diagonal op: later diagonal runs fold into its
     // table while only pure index permutations (X, CNOT, SWAP, Toffoli:
@@ -433,7 +441,7 @@ struct PassBuilder {
                     for (const Pat& pt : pats[ri])
                         if ((pl & pt.lm) == pt.lv && (sel & pt.sm) == pt.sv) e += pt.e;
                 }
-                tabs[o.aux + ((size_t)sel << K) + l] = enc<V>(d * ipow[e & 3], tq62());
+                tabs[o.aux + ((size_t)sel << K) + l] = enc_tab(d * ipow[e & 3]);
             }
         return MERA_OK;
     }
@@ -448,12 +456,24 @@ struct PassBuilder {
     int add_coef(cplx c) { return add_coef(c, i64); }
     int add_coef(cplx c, bool q62) {
         MERA_RETURN_IF(ncoef >= TILE_MAX_COEF, MERA_EUNSUPPORTED, "tile pass coefficient table full");
-        A.coef[ncoef++] = enc<V>(c, q62);
+        A.coef[ncoef++] = engine == ENG_Q ? enc_split(c) : enc<V>(c, q62);
         return MERA_OK;
     }
+    // split Q61 limbs (ENG_Q coefficients and tables), |re|, |im| <= 1
+    static V enc_split(cplx d) {
+        const double sc = 2305843009213693952.0;   // 2^61
+        const long long r = std::llround(d.real() * sc), i = std::llround(d.imag() * sc);
+        const int32_t w[4] = {(int32_t)(r >> 31), (int32_t)(r & 0x7FFFFFFF), (int32_t)(i >> 31),
+                              (int32_t)(i & 0x7FFFFFFF)};
+        V v;
+        memcpy(&v, w, sizeof(V) < sizeof(w) ? sizeof(V) : sizeof(w));
+        return v;
+    }
     // complex128 separable-diagonal tables and their per-tile factors are
-    // Q62 fixed point in both engines (integer multiplies)
+    // Q62 fixed point in every engine (integer multiplies)
     bool tq62() const { return sizeof(V) == 16; }
+    // a table entry: ENG_Q splits each Q61 part into 31-bit limbs
+    V enc_tab(cplx d) const { return engine == ENG_Q ? enc_split(d) : enc<V>(d, tq62()); }
 
     // A run of diagonal gates (they commute): single-qubit factors become one
     // separable diagonal (or exact Z4 terms when all are unit phases), unit-
@@ -593,7 +613,7 @@ struct PassBuilder {
                             const int q = A.tpos[j];
                             if (has[q]) d *= lam[q][(l >> j) & 1];
                         }
-                        tabs[off + (sel << K) + l] = enc<V>(d, tq62());
+                        tabs[off + (sel << K) + l] = enc_tab(d);
                     }
                 }
             }
@@ -751,13 +771,21 @@ struct PassBuilder {
         // others stay in float64 storage, where moves and sign flips are
         // exact and table multiplies run in integer arithmetic
         i64 = allow_i64 && !fp_only && nh > 0;
+        engine = i64 ? ENG_I64 : ENG_FP;
+        if (qres) {
+            i64 = true;
+            engine = ENG_Q;
+        }
         A.scale = std::pow(0.5, nh / 2) * ((nh & 1) ? (1.0 / std::sqrt(2.0)) : 1.0);
         // fixed-point headroom: the max-norm bound (every op's row sum), or
         // for unitary passes the tile 2-norm bound 2^((nh + K) / 2)
         double g = nh + gain_bits;
         if (all_unitary) g = std::min(g, std::ceil((nh + K) / 2.0));
         A.guard = (int)std::ceil(g) + 1;
-        if (A.guard > 28) i64 = false;   // too little fixed-point precision left: float64
+        if (A.guard > 28 && engine == ENG_I64) {   // too little fixed-point precision left: float64
+            i64 = false;
+            engine = ENG_FP;
+        }
         // Merge diagonal runs: a diagonal gate moves past the non-diagonal
         // gates it commutes with (no shared target: a diagonal commutes with
         // gates that only use its qubits as controls), but only when that
@@ -1131,6 +1159,13 @@ struct TileVariant {
 };
 
 static const void* tile_fn_c128(int eng, int feat) {
+    if (eng == ENG_Q) {
+        switch (feat) {
+        case 0: return (const void*)k_tile<double2, ENG_Q, 0>;
+        case FEAT_DIAG: return (const void*)k_tile<double2, ENG_Q, FEAT_DIAG>;
+        default: return (const void*)k_tile<double2, ENG_Q, FEAT_ALL>;
+        }
+    }
     if (eng == ENG_I64) {
         switch (feat) {
         case 0: return (const void*)k_tile<double2, ENG_I64, 0>;
@@ -1187,7 +1222,7 @@ int launch_tile<float2>(int, int, dim3 grid, unsigned block, size_t smem, cudaSt
 // engine and kernel variant per pass, and the diagonal tables.  Passes with
 // `single` >= 0 are per-gate ops (returned in `singles`, -1 otherwise).
 template <typename V>
-int fused_build(int n, const std::vector<PrepOp>& ops, FusedPlan<V>& plan, bool fp_only) {
+int fused_build(int n, const std::vector<PrepOp>& ops, FusedPlan<V>& plan, bool fp_only, bool resident_ok) {
     plan.K = fused_tile_bits(sizeof(V) == 16 ? MERA_C128 : MERA_C64, n);
     plan.n = n;
     const int L = low_bits_for(sizeof(V) == 16 ? MERA_C128 : MERA_C64, plan.K);
@@ -1199,6 +1234,30 @@ int fused_build(int n, const std::vector<PrepOp>& ops, FusedPlan<V>& plan, bool 
     plan.feat.assign(passes.size(), 0);
     plan.single.assign(passes.size(), -1);
     plan.tabs.clear();
+    // resident fixed point: complex128, unitary gates only (the norm bounds
+    // every amplitude), and some arithmetic to gain from it
+    plan.resident = false;
+    plan.qguard = 0;
+    if (sizeof(V) == 16 && !fp_only && resident_ok) {
+        // unitary gates only (the norm bounds every amplitude), some
+        // arithmetic, and every mixing (non-monomial) gate before the first
+        // monomial one: the monomial body keeps each amplitude's magnitude,
+        // so the global scale costs it no precision and nothing later
+        // concentrates rounding errors
+        bool unit = true, arith = false, body = false, mixed_after = false;
+        for (const PrepOp& P : ops) {
+            if (P.kind == KIND_IDENTITY) continue;
+            double rs;
+            bool u;
+            op_gain(P, &rs, &u);
+            unit = unit && u && P.bslot < 0;
+            arith = arith || P.is_h || !op_is_exact(P);
+            const bool monomial = P.kind == KIND_MONO || P.kind == KIND_DIAG;
+            if (monomial) body = true;
+            else if (body) mixed_after = true;
+        }
+        plan.resident = unit && arith && !mixed_after;
+    }
     for (size_t i = 0; i < passes.size(); ++i) {
         if (passes[i].single >= 0) {
             plan.single[i] = passes[i].single;
@@ -1206,11 +1265,129 @@ int fused_build(int n, const std::vector<PrepOp>& ops, FusedPlan<V>& plan, bool 
         }
         PassBuilder<V> b(plan.args[i], plan.tabs, ops, plan.K, n);
         b.fp_only = fp_only;
+        b.qres = plan.resident;
         MERA_TRY(b.build(passes[i], sizeof(V) == 16));
-        plan.eng[i] = b.i64 ? 1 : 0;
+        plan.eng[i] = (unsigned char)b.engine;
+        if (plan.eng[i] == ENG_Q) {
+            // Headroom over the state norm: unnormalised butterflies grow an
+            // amplitude by at most 2^(h/2) for h levels not yet scaled (the
+            // scale is applied at exits once 8 levels are pending, the rest
+            // at the end of the pass); two more bits of slack
+            PassArgs<V>& A = plan.args[i];
+            int pending = 0, most = 0;
+            for (int ph = 0; ph < A.nph; ++ph) {
+                for (int o = A.ph[ph].op_begin; o < A.ph[ph].op_end; ++o) pending += A.ops[o].type == TOP_H;
+                most = std::max(most, pending);
+                A.ph[ph].qsh = 0;
+                if (ph + 1 < A.nph && pending >= 8) {
+                    A.ph[ph].qsh = (int8_t)(pending / 2);
+                    pending -= 2 * (pending / 2);
+                }
+            }
+            A.qend = pending;
+            A.qgi = (most + 1) / 2 + 2;
+            plan.qguard = std::max(plan.qguard, A.qgi);
+        }
         plan.feat[i] = (unsigned char)round_feat(plan.eng[i], b.features(), sizeof(V) == 16);
     }
+    // resident segments: runs of tile passes between per-gate ops; the first
+    // reads doubles, the last writes doubles
+    if (plan.resident) {
+        const size_t np = passes.size();
+        for (size_t i = 0; i < np; ++i) {
+            if (plan.single[i] >= 0) continue;
+            PassArgs<V>& A = plan.args[i];
+            A.q_in = (i > 0 && plan.single[i - 1] < 0) ? 1 : 0;
+            A.q_out = (i + 1 < np && plan.single[i + 1] < 0) ? 1 : 0;
+            A.qgo = A.q_out ? plan.args[i + 1].qgi : A.qgi;
+        }
+    }
     return MERA_OK;
+}
+
+// ------------------------------------------------- resident fixed point --
+// Bound of the squared norm as (E, s): sum of squares < 2^(E - 2046) * s,
+// E = twice the largest exponent field, s accumulated in float32 relative
+// to 2^(E - 2046).  A normal double with exponent field e and mantissa
+// bits m satisfies |x| < (1 + (top 23 bits of m + 1) / 2^23) 2^(e - 1023).
+__device__ __forceinline__ float p2neg(int k) { return k > 126 ? 0.f : __int_as_float((127 - k) << 23); }
+__device__ __forceinline__ void nb_merge(int& E, float& s, int E2, float s2) {
+    if (E2 > E) {
+        s = s * p2neg(E2 - E) + s2;
+        E = E2;
+    } else {
+        s += s2 * p2neg(E - E2);
+    }
+}
+__device__ __forceinline__ void nb_reduce_warp(int& E, float& s) {
+    for (int off = 16; off > 0; off >>= 1) {
+        const int E2 = __shfl_down_sync(0xffffffffu, E, off);
+        const float s2 = __shfl_down_sync(0xffffffffu, s, off);
+        nb_merge(E, s, E2, s2);
+    }
+}
+__global__ void __launch_bounds__(256) k_normbound(const double2* psi, uint64_t N, int* pE, float* pS) {
+    int E = 0;
+    float s = 0.f;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x) {
+        const double2 v = __ldcs(psi + i);
+        const long long bx = __double_as_longlong(v.x), by = __double_as_longlong(v.y);
+        const int ex = (int)((bx >> 52) & 0x7FF), ey = (int)((by >> 52) & 0x7FF);
+        // mantissa factor in [1, 2], rounded up
+        const float fx = __int_as_float(0x3F800000 | (int)((bx >> 29) & 0x7FFFFF)) + 1.1920929e-7f;
+        const float fy = __int_as_float(0x3F800000 | (int)((by >> 29) & 0x7FFFFF)) + 1.1920929e-7f;
+        if (ex) nb_merge(E, s, 2 * ex, fx * fx);
+        if (ey) nb_merge(E, s, 2 * ey, fy * fy);
+    }
+    nb_reduce_warp(E, s);
+    __shared__ int sE[8];
+    __shared__ float sS[8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+        sE[w] = E;
+        sS[w] = s;
+    }
+    __syncthreads();
+    if (w == 0) {
+        E = lane < 8 ? sE[lane] : 0;
+        s = lane < 8 ? sS[lane] : 0.f;
+        nb_reduce_warp(E, s);
+        if (lane == 0) {
+            pE[blockIdx.x] = E;
+            pS[blockIdx.x] = s;
+        }
+    }
+}
+__global__ void k_qscale(const int* pE, const float* pS, int nb, int* outS) {
+    int E = 0;
+    float s = 0.f;
+    for (int b = threadIdx.x; b < nb; b += 32) nb_merge(E, s, pE[b], pS[b]);
+    nb_reduce_warp(E, s);
+    if (threadIdx.x == 0) {
+        int S = 59;
+        if (s > 0.f) {
+            // log2 of the norm bound, with room for float rounding; a pass
+            // with g headroom bits then keeps |component| * 2^(S - g)
+            // below 2^(60 - g)
+            const double l2 = 0.5 * ((double)(E - 2046) + log2((double)s * 1.001));
+            S = 59 - (int)floor(l2);
+        }
+        *outS = S;
+    }
+}
+
+int qscale_launch(const void* psi, int n, void* scratch, cudaStream_t st) {
+    const uint64_t N = 1ull << n;
+    const int nb = (int)std::min<uint64_t>(1024, std::max<uint64_t>(1, N / 1024));
+    char* base = reinterpret_cast<char*>(scratch);
+    launch_begin(st, MERA_KCLASS_REDUCE, (double)N * 16.0);
+    k_normbound<<<nb, 256, 0, st>>>(reinterpret_cast<const double2*>(psi), N, reinterpret_cast<int*>(base),
+                                     reinterpret_cast<float*>(base + 4096));
+    MERA_TRY(launch_end(st));
+    launch_begin(st, MERA_KCLASS_REDUCE, 0.0);
+    k_qscale<<<1, 32, 0, st>>>(reinterpret_cast<const int*>(base), reinterpret_cast<const float*>(base + 4096), nb,
+                               reinterpret_cast<int*>(base + 8192));
+    return launch_end(st);
 }
 
 // Launch pass i of a plan over `ny` states (batch rows).
@@ -1227,8 +1404,8 @@ int fused_launch(const FusedPlan<V>& plan, size_t i, PassArgs<V>& A, unsigned ny
     return launch_end(st);
 }
 
-template int fused_build<double2>(int, const std::vector<PrepOp>&, FusedPlan<double2>&, bool);
-template int fused_build<float2>(int, const std::vector<PrepOp>&, FusedPlan<float2>&, bool);
+template int fused_build<double2>(int, const std::vector<PrepOp>&, FusedPlan<double2>&, bool, bool);
+template int fused_build<float2>(int, const std::vector<PrepOp>&, FusedPlan<float2>&, bool, bool);
 template int fused_launch<double2>(const FusedPlan<double2>&, size_t, PassArgs<double2>&, unsigned, cudaStream_t);
 template int fused_launch<float2>(const FusedPlan<float2>&, size_t, PassArgs<float2>&, unsigned, cudaStream_t);
 
@@ -1276,6 +1453,12 @@ static int upload_plan(mera_state* s, FusedPlan<V>& plan) {
 
 template <typename V>
 static int launch_plan(mera_state* s, FusedPlan<V>& plan, const std::vector<PrepOp>& ops) {
+    if (plan.resident) {
+        MERA_TRY(state_ensure_scratch(s, 16384));
+        MERA_TRY(qscale_launch(s->data, s->n, s->scratch, s->stream));
+        const int* qS = reinterpret_cast<const int*>(reinterpret_cast<char*>(s->scratch) + 8192);
+        for (PassArgs<V>& A : plan.args) A.qS = qS;
+    }
     for (size_t i = 0; i < plan.args.size(); ++i) {
         if (plan.single[i] >= 0) {
             MERA_TRY(apply_prepared(s, ops[plan.single[i]]));
@@ -1291,7 +1474,7 @@ template <typename V>
 static int run_fused(mera_state* s, const std::vector<PrepOp>& ops) {
     fused_cache_free(s);   // the program buffer is about to hold other tables
     FusedPlan<V> plan;
-    MERA_TRY(fused_build<V>(s->n, ops, plan));
+    MERA_TRY(fused_build<V>(s->n, ops, plan, false, true));
     MERA_TRY(upload_plan<V>(s, plan));
     return launch_plan<V>(s, plan, ops);
 }
@@ -1338,7 +1521,7 @@ int apply_fused_circuit(mera_state* s, const mera_op* ops, size_t nops) {
     c->ops.swap(prep);
     int st;
     if (s->dtype == MERA_C128) {
-        st = fused_build<double2>(s->n, c->ops, c->p128);
+        st = fused_build<double2>(s->n, c->ops, c->p128, false, true);
         if (st == MERA_OK) st = upload_plan<double2>(s, c->p128);
     } else {
         st = fused_build<float2>(s->n, c->ops, c->p64);
@@ -1357,42 +1540,44 @@ int apply_fused_circuit(mera_state* s, const mera_op* ops, size_t nops) {
 // Host-only description of the plan (no device work).
 template <typename V>
 static int describe_fused(int n, int dtype, const std::vector<PrepOp>& ops, std::string* out, int* npasses) {
-    const int K = fused_tile_bits(dtype, n);
-    const int L = low_bits_for(dtype, K);
-    std::vector<Pass> passes = plan_passes(ops, n, K, L);
-    std::vector<V> tabs;
-    std::vector<unsigned char> buf(sizeof(PassArgs<V>));
-    PassArgs<V>& A = *reinterpret_cast<PassArgs<V>*>(buf.data());
-    char line[512];
-    snprintf(line, sizeof(line), "K=%d L=%d passes=%zu\n", K, L, passes.size());
+    FusedPlan<V> plan;
+    MERA_TRY(fused_build<V>(n, ops, plan, false, true));
+    const int K = plan.K;
+    char line[640];
+    snprintf(line, sizeof(line), "K=%d L=%d passes=%zu resident=%d qguard=%d table_bytes=%zu\n", K,
+             low_bits_for(dtype, K), plan.args.size(), plan.resident ? 1 : 0, plan.qguard,
+             plan.tabs.size() * sizeof(V));
     *out += line;
-    for (size_t i = 0; i < passes.size(); ++i) {
-        if (passes[i].single >= 0) {
-            snprintf(line, sizeof(line), "pass %zu: per-gate op %d\n", i, passes[i].single);
+    static const char* eng_name[3] = {"fp", "i64", "q"};
+    for (size_t i = 0; i < plan.args.size(); ++i) {
+        if (plan.single[i] >= 0) {
+            snprintf(line, sizeof(line), "pass %zu: per-gate op %d\n", i, plan.single[i]);
             *out += line;
             continue;
         }
-        PassBuilder<V> b(A, tabs, ops, K, n);
-        MERA_TRY(b.build(passes[i], sizeof(V) == 16));
+        const PassArgs<V>& A = plan.args[i];
+        const int nop = A.nph > 0 ? A.ph[A.nph - 1].op_end : 0;
         int cnt[16] = {0};
-        for (int o = 0; o < b.nop; ++o) cnt[A.ops[o].type]++;
+        for (int o = 0; o < nop; ++o) cnt[A.ops[o].type]++;
         std::string bits;
         for (int j = 0; j < K; ++j) bits += std::to_string(A.tpos[j]) + (j + 1 < K ? "," : "");
         std::string dsep;
-        for (int o = 0; o < b.nop; ++o)
+        for (int o = 0; o < nop; ++o)
             if (A.ops[o].type == TOP_DSEP) dsep += " dsep_nontile=" + std::to_string((int)A.ops[o].nt);
         dsep += " phase_ops=[";
         for (int ph = 0; ph < A.nph; ++ph)
             dsep += std::to_string(A.ph[ph].op_end - A.ph[ph].op_begin) + (A.ph[ph].permuted ? "p" : "") +
                     (ph + 1 < A.nph ? "," : "]");
         snprintf(line, sizeof(line),
-                 "pass %zu: eng=%s nh=%d phases=%d ops=%d [g1=%d mono=%d h=%d g2=%d diag=%d dsep=%d z4=%d] "
-                 "guard=%d load_smem=%d store_smem=%d tile={%s}%s\n",
-                 i, b.i64 ? "i64" : "fp", A.nh, A.nph, b.nop, cnt[TOP_G1], cnt[TOP_G1MONO] + cnt[TOP_G2MONO] + cnt[TOP_G1SWAP], cnt[TOP_H],
-                 cnt[TOP_G2], cnt[TOP_DIAG], cnt[TOP_DSEP], cnt[TOP_Z4], A.guard, A.load_smem, A.store_smem, bits.c_str(), dsep.c_str());
+                 "pass %zu: eng=%s feat=%d nh=%d phases=%d ops=%d [g1=%d mono=%d h=%d g2=%d diag=%d dsep=%d z4=%d] "
+                 "guard=%d load_smem=%d store_smem=%d q_in=%d q_out=%d tile={%s}%s\n",
+                 i, eng_name[plan.eng[i] % 3], plan.feat[i], A.nh, A.nph, nop, cnt[TOP_G1],
+                 cnt[TOP_G1MONO] + cnt[TOP_G2MONO] + cnt[TOP_G1SWAP], cnt[TOP_H], cnt[TOP_G2], cnt[TOP_DIAG],
+                 cnt[TOP_DSEP], cnt[TOP_Z4], A.guard, A.load_smem, A.store_smem, A.q_in, A.q_out, bits.c_str(),
+                 dsep.c_str());
         *out += line;
     }
-    if (npasses) *npasses = (int)passes.size();
+    if (npasses) *npasses = (int)plan.args.size();
     return MERA_OK;
 }
 

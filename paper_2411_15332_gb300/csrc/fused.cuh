@@ -16,11 +16,22 @@ struct FusedPlan {
     std::vector<unsigned char> eng, feat;
     std::vector<int> single;              // >= 0: this pass is a per-gate op
     std::vector<V> tabs;                  // diagonal tables to upload (PassArgs::tab)
+    bool resident = false;                // complex128 state kept as int64 fixed point (ENG_Q)
+    int qguard = 0;                       // ENG_Q: headroom bits above the state norm
 };
 
 // fp_only: every pass in the float engine (coefficients as plain values).
+// resident_ok: a complex128 circuit of unitary gates whose mixing gates all
+// precede a monomial body may keep the state in int64 fixed point across
+// its passes (the caller then launches qscale_launch before the first pass
+// and sets PassArgs::qS).
 template <typename V>
-int fused_build(int n, const std::vector<PrepOp>& ops, FusedPlan<V>& plan, bool fp_only = false);
+int fused_build(int n, const std::vector<PrepOp>& ops, FusedPlan<V>& plan, bool fp_only = false,
+                bool resident_ok = false);
+// S = 59 - floor(log2 of a bound of the norm of the complex128 state psi
+// (2^n amplitudes)); a pass with g headroom bits stores value * 2^(S - g).
+// Uses 16 KiB of scratch; S is written to scratch + 8192.
+int qscale_launch(const void* psi, int n, void* scratch, cudaStream_t st);
 template <typename V>
 int fused_launch(const FusedPlan<V>& plan, size_t i, PassArgs<V>& A, unsigned ny, cudaStream_t st);
 

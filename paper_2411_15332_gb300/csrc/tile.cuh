@@ -16,6 +16,18 @@
 // against ~114 FP32 FMAs and ~80 integer adds, so complex128 work avoids
 // FP64 where it can:
 //  * ENG_FP  : float32 arithmetic for complex64 states.
+//  * ENG_Q   : complex128 states held in HBM as int64 fixed point for the
+//              whole run of passes of one circuit (value * 2^(S - g), S
+//              from a bound of the state norm computed on the device, which
+//              unitary passes preserve; g the headroom a pass needs).  Only
+//              the first pass of a run converts from doubles and only the
+//              last converts back; butterflies, moves and sign flips are
+//              exact; table and gate multiplies are 32x32->64 integer
+//              products of 31-bit limbs rounded to nearest; the 2^{-m/2}
+//              Hadamard scale is a shift (times 1/sqrt(2) for odd m).  The
+//              planner uses it for circuits whose mixing gates all precede
+//              a monomial body (phases and permutations keep every
+//              amplitude's magnitude, so a global scale loses nothing).
 //  * ENG_I64 : complex128 states.  The tile is converted once to int64
 //              block floating point (one exponent per tile): butterflies are
 //              exact integer adds, permutations and {1, i, -1, -i} phases are
@@ -41,7 +53,7 @@ constexpr int TILE_MAX_COEF = 448;
 constexpr int TILE_MAX_Z4 = 96;
 constexpr int TILE_MAX_NT = 48;    // non-tile factors of separable diagonals
 
-enum TileEngine { ENG_FP = 0, ENG_I64 = 1 };
+enum TileEngine { ENG_FP = 0, ENG_I64 = 1, ENG_Q = 2 };
 
 // Kernel variants by the op kinds a pass holds (H, monomial 1-target and Z4
 // are always compiled in): fewer op bodies, fewer live registers.
@@ -106,6 +118,7 @@ struct TilePhase {
     int8_t rb[FR];       // local tile bits held in registers, ascending
     int16_t op_begin, op_end;
     int8_t permuted;     // 1: the exit map differs from the entry map (all reads finish first)
+    int8_t qsh;          // ENG_Q: rounded right shift at the exit (part of the 2^(-nh/2) scale)
     XSide in;            // slots this phase reads (from the previous exchange or the load staging)
     XOut out;            // slots this phase writes (next exchange or the store staging)
 };
@@ -126,7 +139,11 @@ struct PassArgs {
     int load_smem;       // 1: stage the first phase's load through shared memory
     int store_smem;      // 1: stage the last phase's store through shared memory
     double scale;        // ENG_FP: applied at the end of the pass
-    int nh;              // Hadamard butterflies in the pass (ENG_I64 scales by 2^-nh/2)
+    int nh;              // Hadamard butterflies in the pass (ENG_I64 / ENG_Q scale by 2^-nh/2)
+    int q_in, q_out;     // ENG_Q: 1 = the state is read / written as fixed point, 0 = as doubles
+    int qgi, qgo;        // ENG_Q: headroom bits of the input / output format (value * 2^(*qS - g))
+    int qend;            // ENG_Q: Hadamard levels still unscaled at the end of the pass
+    const int* qS;       // ENG_Q: device address of S = 59 - floor(log2 of a norm bound)
     int guard;           // ENG_I64: headroom bits of the fixed-point format
     int tpos[16];        // global bit of local bit j, ascending
     XSide ld;            // load staging: slot of element tid + i * 2^(K-FR)
@@ -333,20 +350,79 @@ __device__ __forceinline__ double2 icmul(I2 d, double2 x) {
     return make_double2(fix2d(pr, S), fix2d(pi, S));
 }
 
+// Resident fixed point: a table entry d (|d| <= 1) in Q61, each part split
+// as h * 2^31 + l with 0 <= l < 2^31 (stored as int32 rh, rl, ih, il).
+// For |x| < 2^59 split the same way, x * d / 2^61 is
+// 2 xh dh + (xh dl + xl dh + xl dl / 2^31) / 2^30: six 32x32->64
+// multiply-adds and two 32-bit high products per component, rounded to
+// nearest (error <= 1/2 unit plus 2^-30; zero stays zero, so amplitudes
+// that must vanish do not feed later butterflies).
+__device__ __forceinline__ void qsplit(long long x, int& h, int& l) {
+    h = (int)(x >> 31);
+    l = (int)((unsigned)x & 0x7FFFFFFFu);
+}
+// (a * b) >> 31 for 0 <= a, b < 2^31, to within one unit
+__device__ __forceinline__ long long qlow(int a, int b) { return (long long)(__umulhi((unsigned)a, (unsigned)b) << 1); }
+__device__ __forceinline__ long long qcombine(long long m1, long long m2) {
+    return 2 * m1 + ((m2 + (1ll << 29)) >> 30);
+}
+__device__ __forceinline__ I2 qcmul(int4 d, I2 x) {
+    int rh, rl, ih, il;
+    qsplit(x.x, rh, rl);
+    qsplit(x.y, ih, il);
+    I2 r;
+    // re = xr dr - xi di
+    long long m1 = (long long)rh * d.x - (long long)ih * d.z;
+    long long m2 = (long long)rh * d.y + (long long)rl * d.x - (long long)ih * d.w - (long long)il * d.z +
+                   qlow(rl, d.y) - qlow(il, d.w);
+    r.x = qcombine(m1, m2);
+    // im = xr di + xi dr
+    m1 = (long long)rh * d.z + (long long)ih * d.x;
+    m2 = (long long)rh * d.w + (long long)rl * d.z + (long long)ih * d.y + (long long)il * d.x + qlow(rl, d.w) +
+         qlow(il, d.y);
+    r.y = qcombine(m1, m2);
+    return r;
+}
+// x * c for a real Q61 constant c = ch * 2^31 + cl
+__device__ __forceinline__ long long qmul_real(long long x, int ch, int cl) {
+    int h, l;
+    qsplit(x, h, l);
+    return qcombine((long long)h * ch, (long long)h * cl + (long long)l * ch + qlow(l, cl));
+}
+
 // ------------------------------------------------------------ op bodies --
-template <typename V, int B>
+// Coefficient slot i as split Q61 limbs (ENG_Q coefficient format).
+template <typename V>
+__device__ __forceinline__ int4 qcoef(const V* cf, int i) {
+    return *reinterpret_cast<const int4*>(cf + i);
+}
+
+template <typename V, int B, int ENG>
 __device__ __forceinline__ void op_g1(V (&x)[FRA], const TileOp& o, const V* cf, uint64_t gb, const uint64_t* gm) {
     const uint32_t act = active16(o.cmask, o.cvals, gb, gm);
     if (act == 0) return;
-    const V m0 = cf[0], m1 = cf[1], m2 = cf[2], m3 = cf[3];
+    if constexpr (ENG == ENG_Q) {
+        const int4 q0 = qcoef(cf, 0), q1 = qcoef(cf, 1), q2 = qcoef(cf, 2), q3 = qcoef(cf, 3);
 #pragma unroll
-    for (int j = 0; j < FRA; ++j) {
-        if (j & (1 << B)) continue;
-        const int j1 = j | (1 << B);
-        if (!(act & (1u << j))) continue;
-        const V a0 = x[j], a1 = x[j1];
-        x[j] = cdot2(m0, a0, m1, a1);
-        x[j1] = cdot2(m2, a0, m3, a1);
+        for (int j = 0; j < FRA; ++j) {
+            if (j & (1 << B)) continue;
+            const int j1 = j | (1 << B);
+            if (!(act & (1u << j))) continue;
+            const V a0 = x[j], a1 = x[j1];
+            x[j] = vadd(qcmul(q0, a0), qcmul(q1, a1));
+            x[j1] = vadd(qcmul(q2, a0), qcmul(q3, a1));
+        }
+    } else {
+        const V m0 = cf[0], m1 = cf[1], m2 = cf[2], m3 = cf[3];
+#pragma unroll
+        for (int j = 0; j < FRA; ++j) {
+            if (j & (1 << B)) continue;
+            const int j1 = j | (1 << B);
+            if (!(act & (1u << j))) continue;
+            const V a0 = x[j], a1 = x[j1];
+            x[j] = cdot2(m0, a0, m1, a1);
+            x[j1] = cdot2(m2, a0, m3, a1);
+        }
     }
 }
 
@@ -394,7 +470,7 @@ __device__ __forceinline__ void op_h(V (&x)[FRA]) {
     }
 }
 
-template <typename V, int A, int B>
+template <typename V, int A, int B, int ENG>
 __device__ __forceinline__ void op_g2(V (&x)[FRA], const TileOp& o, const V* cf, uint64_t gb, const uint64_t* gm,
                                       bool mono) {
     const uint32_t act = active16(o.cmask, o.cvals, gb, gm);
@@ -417,6 +493,14 @@ __device__ __forceinline__ void op_g2(V (&x)[FRA], const TileOp& o, const V* cf,
                     if (src == u) v = in[u];
                 x[id[s]] = mul_ik(v, code_at(o.codes, s) & 3);
             }
+        } else if constexpr (ENG == ENG_Q) {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                V acc = qcmul(qcoef(cf, r * 4), in[0]);
+#pragma unroll
+                for (int c = 1; c < 4; ++c) acc = vadd(acc, qcmul(qcoef(cf, r * 4 + c), in[c]));
+                x[id[r]] = acc;
+            }
         } else {
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
@@ -429,7 +513,7 @@ __device__ __forceinline__ void op_g2(V (&x)[FRA], const TileOp& o, const V* cf,
     }
 }
 
-template <typename V>
+template <typename V, int ENG>
 __device__ __forceinline__ void op_diag(V (&x)[FRA], const TileOp& o, const V* cf, uint64_t gb, const uint64_t* gm) {
     const uint32_t act = active16(o.cmask, o.cvals, gb, gm);
     if (act == 0) return;
@@ -439,7 +523,13 @@ __device__ __forceinline__ void op_diag(V (&x)[FRA], const TileOp& o, const V* c
         const uint64_t g = gb | dep4(j, gm);
         int sub = 0;
         for (int t = 0; t < o.nt; ++t) sub = (sub << 1) | (int)((g >> o.tq[t]) & 1ull);
-        if ((o.flags >> sub) & 1u) x[j] = phase_any(code_at(o.codes, sub), cf[sub], x[j]);
+        if (!((o.flags >> sub) & 1u)) continue;
+        const int code = code_at(o.codes, sub);
+        if constexpr (ENG == ENG_Q) {
+            x[j] = code < 4 ? mul_ik(x[j], code) : qcmul(qcoef(cf, sub), x[j]);
+        } else {
+            x[j] = phase_any(code, cf[sub], x[j]);
+        }
     }
 }
 
@@ -470,13 +560,34 @@ __device__ __forceinline__ void op_z4(V (&x)[FRA], const TileOp& o, const Z4Term
 // the remaining non-tile factors multiply in per tile.
 constexpr int DSEP_SEL_BITS = 3;
 
-template <typename V>
+template <typename V, int ENG>
 __device__ __forceinline__ void op_dsep(V (&x)[FRA], const TileOp& o, const V* cf, const V* tab, const int8_t* ntq,
                                         uint32_t lb, const int* lm, uint64_t gb, int K) {
     const int nsel = o.nt < DSEP_SEL_BITS ? o.nt : DSEP_SEL_BITS;
     uint32_t sel = 0;
     for (int f = 0; f < nsel; ++f) sel |= (uint32_t)((gb >> ntq[o.aux2 + f]) & 1ull) << f;
-    if constexpr (std::is_same<V, double2>::value) {
+    if constexpr (ENG == ENG_Q) {
+        // split-Q61 tables; per-tile factors (Q62) multiply separately
+        const int4* t = reinterpret_cast<const int4*>(tab) + o.aux + ((size_t)sel << K);
+        // groups of four entries in flight (an empty asm with a memory
+        // clobber keeps the compiler from hoisting all sixteen loads)
+#pragma unroll
+        for (int g = 0; g < FRA; g += 4) {
+            int4 d[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) d[u] = __ldg(t + (lb | dep4(g + u, lm)));
+#pragma unroll
+            for (int u = 0; u < 4; ++u) x[g + u] = qcmul(d[u], x[g + u]);
+            asm volatile("" ::: "memory");
+        }
+        // per-tile factors: each multiplies every amplitude in turn
+        for (int f = nsel; f < o.nt; ++f) {
+            if (!((gb >> ntq[o.aux2 + f]) & 1ull)) continue;
+            const int4 c = qcoef(cf, f - nsel);
+#pragma unroll
+            for (int j = 0; j < FRA; ++j) x[j] = qcmul(c, x[j]);
+        }
+    } else if constexpr (std::is_same<V, double2>::value) {
         // complex128 in the float engine: Q62 tables and factors, integer
         // multiplies (no FP64 instruction)
         const I2* t = reinterpret_cast<const I2*>(tab) + o.aux + ((size_t)sel << K);
@@ -515,16 +626,16 @@ __device__ __forceinline__ void op_dsep(V (&x)[FRA], const TileOp& o, const V* c
     }
 }
 
-template <typename V, typename SV, int FEAT>
+template <typename V, typename SV, int ENG, int FEAT>
 __device__ __forceinline__ void apply_tile_op(V (&x)[FRA], const TileOp& o, const PassArgs<SV>& a, const V* cf,
                                               uint64_t gb, const uint64_t* gm, uint32_t lb, const int* lm) {
     switch (o.type) {
     case TOP_G1:
         if constexpr ((FEAT & FEAT_DENSE1) != 0) switch (o.a) {
-        case 0: op_g1<V, 0>(x, o, cf, gb, gm); break;
-        case 1: op_g1<V, 1>(x, o, cf, gb, gm); break;
-        case 2: op_g1<V, 2>(x, o, cf, gb, gm); break;
-        default: op_g1<V, 3>(x, o, cf, gb, gm); break;
+        case 0: op_g1<V, 0, ENG>(x, o, cf, gb, gm); break;
+        case 1: op_g1<V, 1, ENG>(x, o, cf, gb, gm); break;
+        case 2: op_g1<V, 2, ENG>(x, o, cf, gb, gm); break;
+        default: op_g1<V, 3, ENG>(x, o, cf, gb, gm); break;
         }
         break;
     case TOP_G1MONO:
@@ -555,22 +666,22 @@ __device__ __forceinline__ void apply_tile_op(V (&x)[FRA], const TileOp& o, cons
     case TOP_G2MONO: {
         const bool mono = o.type == TOP_G2MONO;
         if constexpr ((FEAT & FEAT_G2) != 0) switch (o.a * 4 + o.b) {
-        case 1 * 4 + 0: op_g2<V, 1, 0>(x, o, cf, gb, gm, mono); break;
-        case 2 * 4 + 0: op_g2<V, 2, 0>(x, o, cf, gb, gm, mono); break;
-        case 2 * 4 + 1: op_g2<V, 2, 1>(x, o, cf, gb, gm, mono); break;
-        case 3 * 4 + 0: op_g2<V, 3, 0>(x, o, cf, gb, gm, mono); break;
-        case 3 * 4 + 1: op_g2<V, 3, 1>(x, o, cf, gb, gm, mono); break;
-        default: op_g2<V, 3, 2>(x, o, cf, gb, gm, mono); break;
+        case 1 * 4 + 0: op_g2<V, 1, 0, ENG>(x, o, cf, gb, gm, mono); break;
+        case 2 * 4 + 0: op_g2<V, 2, 0, ENG>(x, o, cf, gb, gm, mono); break;
+        case 2 * 4 + 1: op_g2<V, 2, 1, ENG>(x, o, cf, gb, gm, mono); break;
+        case 3 * 4 + 0: op_g2<V, 3, 0, ENG>(x, o, cf, gb, gm, mono); break;
+        case 3 * 4 + 1: op_g2<V, 3, 1, ENG>(x, o, cf, gb, gm, mono); break;
+        default: op_g2<V, 3, 2, ENG>(x, o, cf, gb, gm, mono); break;
         }
         break;
     }
     case TOP_DIAG:
-        if constexpr ((FEAT & FEAT_DIAG) != 0) op_diag<V>(x, o, cf, gb, gm);
+        if constexpr ((FEAT & FEAT_DIAG) != 0) op_diag<V, ENG>(x, o, cf, gb, gm);
         break;
     case TOP_Z4: op_z4<V>(x, o, a.z4, gb, gm); break;
     default:
         if constexpr ((FEAT & FEAT_DIAG) != 0)
-            op_dsep<V>(x, o, cf, reinterpret_cast<const V*>(a.tab), a.ntq, lb, lm, gb, a.K);
+            op_dsep<V, ENG>(x, o, cf, reinterpret_cast<const V*>(a.tab), a.ntq, lb, lm, gb, a.K);
         break;
     }
 }
@@ -596,9 +707,9 @@ __device__ __forceinline__ V raw_load(const SV v) {
 // registers, no spills) when multiplying op bodies are compiled in.
 template <typename SV, int ENG, int FEAT>
 __global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
-                                  (sizeof(SV) == 16 && (FEAT == 0 || (ENG == ENG_FP && FEAT == FEAT_DIAG))) ? 2 : 1)
+                                  (sizeof(SV) == 16 && (FEAT == 0 || (ENG != ENG_I64 && FEAT == FEAT_DIAG))) ? 2 : 1)
     k_tile(const __grid_constant__ PassArgs<SV> a) {
-    using V = typename std::conditional<ENG == ENG_I64, I2, SV>::type;
+    using V = typename std::conditional<ENG == ENG_FP, SV, I2>::type;
     constexpr int EB = sizeof(SV);
     extern __shared__ __align__(16) unsigned char smraw[];
     SV* sms = reinterpret_cast<SV*>(smraw);     // staging of stored values
@@ -612,7 +723,8 @@ __global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
     SV* const psi = a.psi + (a.slots ? (unsigned long long)a.slots[blockIdx.y] : (unsigned long long)blockIdx.y) * a.bstride;
     const V* const bcf = reinterpret_cast<const V*>(a.bcoef) + (size_t)blockIdx.y * a.bcstride;
     V x[FRA];
-    int S = 0;   // ENG_I64: fixed-point exponent
+    int S = 0;   // ENG_I64 / ENG_Q: fixed-point exponent
+    if constexpr (ENG == ENG_Q) S = *a.qS - a.qgi;
 
     if (a.load_smem) {
         // coalesced copy: element tid + i*T, its top FR local bits come from i
@@ -651,6 +763,15 @@ __global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
 #pragma unroll
                 for (int j = 0; j < FRA; ++j) x[j] = raw_load<SV, V>(sms[sb ^ dep4x(j, sr)]);
             }
+            if constexpr (ENG == ENG_Q) {
+                if (!a.q_in) {
+#pragma unroll
+                    for (int j = 0; j < FRA; ++j) {
+                        x[j].x = d2fix(__longlong_as_double(x[j].x), S);
+                        x[j].y = d2fix(__longlong_as_double(x[j].y), S);
+                    }
+                }
+            }
             if constexpr (ENG == ENG_I64) {
                 // tile exponent: max over the tile of both components
                 int e = 0;
@@ -678,7 +799,7 @@ __global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
         for (int o = ph.op_begin; o < ph.op_end; ++o) {
             const TileOp& op = a.ops[o];
             const V* cf = (op.c ? bcf : reinterpret_cast<const V*>(a.coef)) + op.coef;
-            apply_tile_op<V, SV, FEAT>(x, op, a, cf, gb, gm, lb, lm);
+            apply_tile_op<V, SV, ENG, FEAT>(x, op, a, cf, gb, gm, lb, lm);
         }
         // exit slots: the same as the entry slots unless the exchange
         // permutes the tile index, in which case every read of this phase
@@ -694,6 +815,17 @@ __global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
             for (int r = 0; r < FR; ++r) orr[r] = sr[r];
         }
         if (p != a.nph - 1) {
+            if constexpr (ENG == ENG_Q) {
+                if (ph.qsh > 0) {
+                    const int k = ph.qsh;
+                    const long long half = 1ll << (k - 1);
+#pragma unroll
+                    for (int j = 0; j < FRA; ++j) {
+                        x[j].x = (x[j].x + half) >> k;
+                        x[j].y = (x[j].y + half) >> k;
+                    }
+                }
+            }
 #pragma unroll
             for (int j = 0; j < FRA; ++j) sm[ob ^ dep4x(j, orr)] = x[j];
             __syncthreads();
@@ -701,7 +833,37 @@ __global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
         }
         // last phase: back to the storage type, then out
         SV* out = reinterpret_cast<SV*>(x);
-        if constexpr (ENG == ENG_I64) {
+        if constexpr (ENG == ENG_Q) {
+            // the pass's 2^(-nh/2) and the change to the next pass's format
+            // (S_out - S_in = qgi - qgo): one rounded shift, times 1/sqrt(2)
+            // for odd nh; then doubles unless the state stays fixed point
+            const int k = (a.qend >> 1) + (a.q_out ? a.qgo - a.qgi : 0);
+            const bool odd = a.qend & 1;
+            const long long half = k > 0 ? (1ll << (k - 1)) : 0ll;
+            const int r2h = 759250124, r2l = 2134625280;   // round(2^61 / sqrt(2)) = r2h * 2^31 + r2l
+#pragma unroll
+            for (int j = 0; j < FRA; ++j) {
+                long long vx = x[j].x, vy = x[j].y;
+                if (odd) {
+                    vx = qmul_real(vx, r2h, r2l);
+                    vy = qmul_real(vy, r2h, r2l);
+                }
+                if (k > 0) {
+                    vx = (vx + half) >> k;
+                    vy = (vy + half) >> k;
+                } else if (k < 0) {
+                    vx = (long long)((unsigned long long)vx << (-k));
+                    vy = (long long)((unsigned long long)vy << (-k));
+                }
+                if (a.q_out) {
+                    x[j].x = vx;
+                    x[j].y = vy;
+                } else {
+                    x[j].x = __double_as_longlong(fix2d(vx, S));
+                    x[j].y = __double_as_longlong(fix2d(vy, S));
+                }
+            }
+        } else if constexpr (ENG == ENG_I64) {
             // undo the fixed-point scale and apply 2^(-nh/2)
             const int So = S + (a.nh >> 1);
             const bool odd = a.nh & 1;

@@ -1,0 +1,82 @@
+"""The complex128 fused path keeps the state as int64 fixed point across a
+circuit's tile passes (global scale from a norm bound).  These tests pin
+what that format must preserve: exact results where the mathematics gives
+exact values, exact zeros, the norm over long circuits, and states that are
+not normalised."""
+import numpy as np
+import pytest
+
+from oracle import statevector as sv
+from paper_2411_15332_gb300 import inputs
+from paper_2411_15332_gb300.inputs import op
+from tests.gpu_helpers import lib_ready, max_err, new_state
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _ready():
+    lib_ready()
+
+
+@pytest.mark.parametrize("n", [20, 21, 24, 25])
+def test_hadamard_layer_is_uniform(n):
+    """H on every qubit of |0>: every amplitude is 2^(-n/2) (exact for even
+    n, within a few units in the last place for odd n)."""
+    s = new_state(n)
+    s.apply_circuit(inputs.hadamard_all(n), mode="fused")
+    got = s.to_numpy()
+    s.close()
+    exact = 2.0 ** (-n / 2)
+    assert np.max(np.abs(got.imag)) == 0.0
+    assert np.max(np.abs(got.real - exact)) <= 1e-14 * exact
+
+
+def test_vanishing_amplitudes_stay_exactly_zero():
+    """H on qubits 0..20 of n = 24 (two passes, one with an odd number of
+    levels): amplitudes with any of bits 21..23 set are exactly 0."""
+    n = 24
+    s = new_state(n)
+    s.apply_circuit([op("H", (q,)) for q in range(21)], mode="fused")
+    got = s.to_numpy()
+    s.close()
+    idx = np.arange(1 << n)
+    assert np.all(got[(idx >> 21) != 0] == 0)
+    assert np.max(np.abs(got[(idx >> 21) == 0] - 2.0 ** -10.5)) <= 1e-14 * 2.0 ** -10.5
+
+
+def test_norm_and_probabilities_over_a_long_circuit():
+    """Layered circuit, n = 22, 20 layers (61 passes): after the H layer
+    every gate is a phase times a permutation, so every probability stays
+    2^-n, the norm stays 1 and <Z_0> = 0."""
+    n = 22
+    ops = inputs.layered_circuit(n, 20, seed=2)
+    s = new_state(n)
+    s.apply_circuit(ops, mode="fused")
+    got = s.to_numpy()
+    nrm, z0, _ = s.observables(0)
+    s.close()
+    assert abs(nrm - 1.0) <= 1e-13
+    assert abs(z0) <= 1e-13
+    assert np.max(np.abs(np.abs(got) ** 2 * (1 << n) - 1.0)) <= 1e-11
+    ref = sv.simulate(n, ops)
+    assert max_err(got, ref) <= 1e-13
+
+
+@pytest.mark.parametrize("scale", [1e-3, 3.7, 1e5])
+def test_unnormalised_state(scale):
+    """The format's scale follows the state's norm: a random state times
+    `scale` through rotations on every qubit followed by a monomial body
+    (CNOT ladders, CZ, T/S, RZ) matches the oracle within 1e-12 relative to
+    the norm."""
+    n = 14
+    psi = inputs.random_state(n, seed=9) * scale
+    rng = np.random.default_rng(10)
+    prefix = [op("RY", (q,), (), (float(rng.uniform(0, 6.28)),)) for q in range(n)]
+    ops = prefix + inputs.layered_circuit(n, 6, seed=11)[n:]
+    s = new_state(n, psi=psi)
+    s.apply_circuit(ops, mode="fused")
+    got = s.to_numpy()
+    s.close()
+    ref = sv.simulate(n, ops, psi0=psi)
+    assert max_err(got, ref) <= 1e-12 * scale

@@ -1,0 +1,88 @@
+"""Host-side planning of the fused tile passes (no GPU): which engine each
+pass runs, that CNOT/X/SWAP runs become exchange index maps instead of
+register ops, the per-pass Hadamard cap, and when the complex128 state is
+kept as fixed point across passes.  CPU only."""
+import re
+
+import numpy as np
+import pytest
+
+from paper_2411_15332_gb300 import inputs
+from paper_2411_15332_gb300.inputs import op
+
+
+@pytest.fixture(scope="module")
+def core():
+    from paper_2411_15332_gb300.build import build
+    build()
+    from paper_2411_15332_gb300 import core as c
+    return c
+
+
+def parse(summary):
+    head = summary.splitlines()[0]
+    info = dict(re.findall(r"(\w+)=(\d+)", head))
+    passes = []
+    for line in summary.splitlines()[1:]:
+        if "per-gate" in line:
+            passes.append({"single": True})
+            continue
+        d = dict(re.findall(r"(\w+)=([\w\d]+)", line.split("tile=")[0]))
+        d["phase_ops"] = re.search(r"phase_ops=\[([^\]]*)\]", line).group(1)
+        passes.append(d)
+    return {k: int(v) for k, v in info.items()}, passes
+
+
+def test_layered_n30_plan(core):
+    head, passes = parse(core.plan_summary(30, inputs.layered_circuit(30, 20, seed=2)))
+    assert head["resident"] == 1 and head["passes"] == 60
+    assert all(p["eng"] == "q" for p in passes)
+    # the CNOT ladders ride on the exchanges: no register permutation op
+    assert all(p["mono"] == "0" for p in passes)
+    # at most one separable-diagonal table per pass
+    assert all(int(p["dsep"]) <= 2 for p in passes)
+    # the resident run converts from doubles once and back once
+    assert passes[0]["q_in"] == "0" and passes[-1]["q_out"] == "0"
+    assert all(p["q_in"] == "1" for p in passes[1:]) and all(p["q_out"] == "1" for p in passes[:-1])
+
+
+def test_hadamard_levels_per_pass_are_capped(core):
+    ops, _ = inputs.grover_circuit(12, 8, seed=3)
+    head, passes = parse(core.plan_summary(12, ops))
+    assert all(int(p["nh"]) <= 16 for p in passes)
+    assert sum(int(p["nh"]) for p in passes) == 12 * 17
+
+
+def test_non_unitary_gate_disables_resident_format(core):
+    n = 12
+    m = np.diag([2.0, 0.5]).astype(np.complex128)
+    ops = inputs.hadamard_all(n) + [(m, (3,), (), (), 0)]   # an explicit (non-unitary) matrix
+    head, passes = parse(core.plan_summary(n, ops))
+    assert head["resident"] == 0
+    assert all(p.get("eng") != "q" for p in passes if not p.get("single"))
+
+
+def test_exact_only_circuit_stays_in_float64(core):
+    """Permutations and unit phases only: exact moves in float64, no
+    fixed-point round trip."""
+    n = 20
+    ops = [op("X", (q + 1,), (q,)) for q in range(n - 1)] + [op("S", (q,)) for q in range(n)]
+    head, passes = parse(core.plan_summary(n, ops))
+    assert head["resident"] == 0
+    assert all(p["eng"] == "fp" for p in passes)
+
+
+def test_complex64_plans_use_the_float_engine(core):
+    head, passes = parse(core.plan_summary(24, inputs.layered_circuit(24, 3, seed=2), dtype="c64"))
+    assert head["resident"] == 0
+    assert all(p["eng"] == "fp" for p in passes)
+
+
+def test_mixing_gates_after_the_body_keep_doubles(core):
+    """Grover: Hadamard layers after phase flips -- a global fixed-point
+    scale would let later butterflies concentrate rounding errors, so the
+    passes keep double storage (per-tile int64 for the butterflies)."""
+    ops, _ = inputs.grover_circuit(24, 4, seed=3)
+    head, passes = parse(core.plan_summary(24, ops))
+    assert head["resident"] == 0
+    assert all(p["eng"] in ("i64", "fp") for p in passes)
