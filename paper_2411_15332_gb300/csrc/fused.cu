@@ -22,6 +22,7 @@
 
 #include "common.cuh"
 #include "fused.cuh"
+#include "tile_fns.cuh"
 
 namespace mera {
 
@@ -732,6 +733,9 @@ struct PassBuilder {
             case TOP_G2MONO: f |= FEAT_G2; break;
             case TOP_DIAG:
             case TOP_DSEP: f |= FEAT_DIAG; break;
+            case TOP_H:
+            case TOP_G1MONO:
+            case TOP_G1SWAP: f |= FEAT_GATES; break;
             default: break;
             }
         }
@@ -1158,33 +1162,18 @@ struct TileVariant {
     int eng, feat;
 };
 
-static const void* tile_fn_c128(int eng, int feat) {
-    if (eng == ENG_Q) {
-        switch (feat) {
-        case 0: return (const void*)k_tile<double2, ENG_Q, 0>;
-        case FEAT_DIAG: return (const void*)k_tile<double2, ENG_Q, FEAT_DIAG>;
-        default: return (const void*)k_tile<double2, ENG_Q, FEAT_ALL>;
-        }
-    }
-    if (eng == ENG_I64) {
-        switch (feat) {
-        case 0: return (const void*)k_tile<double2, ENG_I64, 0>;
-        case FEAT_DIAG: return (const void*)k_tile<double2, ENG_I64, FEAT_DIAG>;
-        default: return (const void*)k_tile<double2, ENG_I64, FEAT_ALL>;
-        }
-    }
-    switch (feat) {
-    case 0: return (const void*)k_tile<double2, ENG_FP, 0>;
-    case FEAT_DIAG: return (const void*)k_tile<double2, ENG_FP, FEAT_DIAG>;
-    default: return (const void*)k_tile<double2, ENG_FP, FEAT_ALL>;
-    }
+static const void* tile_fn_c128(int eng, int feat, int qin) {
+    if (eng == ENG_Q) return tile_fn_q(feat, qin);
+    if (eng == ENG_I64) return tile_fn_i64(feat, 0);
+    return tile_fn_fp(feat, 0);
 }
 
 // Smallest compiled variant that covers the requested features.
 static int round_feat(int, int feat, bool c128) {
     if (!c128) return FEAT_ALL;
-    if (feat == 0) return 0;
-    if (feat == FEAT_DIAG) return FEAT_DIAG;
+    if (feat == 0 || feat == FEAT_DIAG) return FEAT_DIAG;   // sign terms only: the leanest body
+    if (feat == FEAT_GATES) return FEAT_GATES;
+    if (feat == (FEAT_GATES | FEAT_DIAG)) return FEAT_GATES | FEAT_DIAG;
     return FEAT_ALL;
 }
 
@@ -1194,7 +1183,7 @@ static int launch_tile(int eng, int feat, dim3 grid, unsigned block, size_t smem
 template <>
 int launch_tile<double2>(int eng, int feat, dim3 grid, unsigned block, size_t smem, cudaStream_t st,
                          const PassArgs<double2>& A) {
-    const void* fn = tile_fn_c128(eng, feat);
+    const void* fn = tile_fn_c128(eng, feat, eng == ENG_Q && !A.q_in ? 1 : 0);
     // opt in to the tile's dynamic shared memory (once per variant and size)
     static std::vector<std::pair<const void*, size_t>> opted;
     if (smem > 48 * 1024 && std::find(opted.begin(), opted.end(), std::make_pair(fn, smem)) == opted.end()) {
@@ -1210,11 +1199,11 @@ int launch_tile<float2>(int, int, dim3 grid, unsigned block, size_t smem, cudaSt
                         const PassArgs<float2>& A) {
     static size_t opted = 0;
     if (smem > 48 * 1024 && smem > opted) {
-        MERA_CHECK_CUDA(cudaFuncSetAttribute(k_tile<float2, ENG_FP, FEAT_ALL>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        MERA_CHECK_CUDA(cudaFuncSetAttribute(tile_fn_c64(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         opted = smem;
     }
-    k_tile<float2, ENG_FP, FEAT_ALL><<<grid, block, smem, st>>>(A);
+    void* args[] = {const_cast<PassArgs<float2>*>(&A)};
+    MERA_CHECK_CUDA(cudaLaunchKernel(tile_fn_c64(), grid, dim3(block), args, smem, st));
     return MERA_OK;
 }
 

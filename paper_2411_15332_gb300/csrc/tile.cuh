@@ -55,9 +55,10 @@ constexpr int TILE_MAX_NT = 48;    // non-tile factors of separable diagonals
 
 enum TileEngine { ENG_FP = 0, ENG_I64 = 1, ENG_Q = 2 };
 
-// Kernel variants by the op kinds a pass holds (H, monomial 1-target and Z4
-// are always compiled in): fewer op bodies, fewer live registers.
-enum TileFeature { FEAT_DIAG = 1, FEAT_DENSE1 = 2, FEAT_G2 = 4, FEAT_ALL = 7 };
+// Kernel variants by the op kinds a pass holds (Z4 terms are always
+// compiled in; FEAT_GATES: Hadamard butterflies and one-target monomials):
+// fewer op bodies, fewer live registers, less instruction cache.
+enum TileFeature { FEAT_DIAG = 1, FEAT_DENSE1 = 2, FEAT_G2 = 4, FEAT_GATES = 8, FEAT_ALL = 15 };
 
 enum TileOpType : int8_t {
     TOP_G1 = 0,       // dense 2x2 on one register bit (coef[0..3])
@@ -639,7 +640,7 @@ __device__ __forceinline__ void apply_tile_op(V (&x)[FRA], const TileOp& o, cons
         }
         break;
     case TOP_G1MONO:
-        switch (o.a) {
+        if constexpr ((FEAT & FEAT_GATES) != 0) switch (o.a) {
         case 0: op_g1mono<V, 0>(x, o, cf, gb, gm); break;
         case 1: op_g1mono<V, 1>(x, o, cf, gb, gm); break;
         case 2: op_g1mono<V, 2>(x, o, cf, gb, gm); break;
@@ -647,7 +648,7 @@ __device__ __forceinline__ void apply_tile_op(V (&x)[FRA], const TileOp& o, cons
         }
         break;
     case TOP_G1SWAP:
-        switch (o.a) {
+        if constexpr ((FEAT & FEAT_GATES) != 0) switch (o.a) {
         case 0: op_g1swap<V, 0>(x, o, gb, gm); break;
         case 1: op_g1swap<V, 1>(x, o, gb, gm); break;
         case 2: op_g1swap<V, 2>(x, o, gb, gm); break;
@@ -655,7 +656,7 @@ __device__ __forceinline__ void apply_tile_op(V (&x)[FRA], const TileOp& o, cons
         }
         break;
     case TOP_H:
-        switch (o.a) {
+        if constexpr ((FEAT & FEAT_GATES) != 0) switch (o.a) {
         case 0: op_h<V, 0>(x); break;
         case 1: op_h<V, 1>(x); break;
         case 2: op_h<V, 2>(x); break;
@@ -705,9 +706,13 @@ __device__ __forceinline__ V raw_load(const SV v) {
 // op kinds compiled in.
 // complex128: two CTAs per SM for the lightest variant, one (with up to 255
 // registers, no spills) when multiplying op bodies are compiled in.
-template <typename SV, int ENG, int FEAT>
+// QIN (ENG_Q only): 1 = this pass converts its input from doubles (the
+// first pass of a fixed-point run); a separate instantiation keeps the
+// conversion's registers out of the other passes.
+template <typename SV, int ENG, int FEAT, int QIN = 0>
 __global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
-                                  (sizeof(SV) == 16 && (FEAT == 0 || (ENG != ENG_I64 && FEAT == FEAT_DIAG))) ? 2 : 1)
+                                  (sizeof(SV) == 16 && (FEAT == FEAT_GATES || FEAT == FEAT_DIAG ||
+                                                        (ENG != ENG_I64 && FEAT == (FEAT_GATES | FEAT_DIAG)))) ? 2 : 1)
     k_tile(const __grid_constant__ PassArgs<SV> a) {
     using V = typename std::conditional<ENG == ENG_FP, SV, I2>::type;
     constexpr int EB = sizeof(SV);
@@ -763,13 +768,11 @@ __global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
 #pragma unroll
                 for (int j = 0; j < FRA; ++j) x[j] = raw_load<SV, V>(sms[sb ^ dep4x(j, sr)]);
             }
-            if constexpr (ENG == ENG_Q) {
-                if (!a.q_in) {
+            if constexpr (ENG == ENG_Q && QIN == 1) {
 #pragma unroll
-                    for (int j = 0; j < FRA; ++j) {
-                        x[j].x = d2fix(__longlong_as_double(x[j].x), S);
-                        x[j].y = d2fix(__longlong_as_double(x[j].y), S);
-                    }
+                for (int j = 0; j < FRA; ++j) {
+                    x[j].x = d2fix(__longlong_as_double(x[j].x), S);
+                    x[j].y = d2fix(__longlong_as_double(x[j].y), S);
                 }
             }
             if constexpr (ENG == ENG_I64) {

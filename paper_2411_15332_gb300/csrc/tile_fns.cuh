@@ -1,0 +1,17 @@
+// Entry points of the tile-kernel variants (one translation unit per
+// engine: tile_q.cu, tile_i64.cu, tile_fp.cu).
+#pragma once
+
+#include "tile.cuh"
+
+namespace mera {
+
+// complex128 kernels by engine and feature set; qin = 1 selects the
+// fixed-point variant that converts its input from doubles
+const void* tile_fn_q(int feat, int qin);
+const void* tile_fn_i64(int feat, int qin);
+const void* tile_fn_fp(int feat, int qin);
+// the complex64 kernel
+const void* tile_fn_c64();
+
+}  // namespace mera
