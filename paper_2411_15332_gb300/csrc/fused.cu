@@ -993,24 +993,36 @@ struct PassBuilder {
         const int save_nop = nop, save_ncoef = ncoef, save_nz4 = nz4, save_nnt = nnt;
         const size_t save_tabs = tabs.size();
         const OpenTable save_ot = ot;
-        const int r = build_phases_with(p, true);
+        auto restore = [&]() {
+            nop = save_nop;
+            ncoef = save_ncoef;
+            nz4 = save_nz4;
+            nnt = save_nnt;
+            tabs.resize(save_tabs);
+            ot = save_ot;
+            A.gather = A.scatter = 0;
+        };
+        // permutation runs at the ends of the pass on the load / store
+        // addresses, the others on exchanges; then exchanges only; then
+        // register ops (too many phases or exchange offsets)
+        int r = build_phases_with(p, true, true);
         if (r == MERA_OK) return r;
-        // too many phases or exit offsets with absorbed permutations: run
-        // every permutation as a register op
-        nop = save_nop;
-        ncoef = save_ncoef;
-        nz4 = save_nz4;
-        nnt = save_nnt;
-        tabs.resize(save_tabs);
-        ot = save_ot;
-        return build_phases_with(p, false);
+        restore();
+        r = build_phases_with(p, true, false);
+        if (r == MERA_OK) return r;
+        restore();
+        return build_phases_with(p, false, false);
     }
 
-    int build_phases_with(const Pass& p, bool absorb) {
+    int build_phases_with(const Pass& p, bool absorb, bool gs) {
         // phases: consecutive gates while their targets fit FR register
         // bits; a run of absorbable permutations ends the phase and becomes
-        // its exit map (runs of one gate only at a phase start or the end)
+        // its exit map (runs of one gate only at a phase start or the end);
+        // with gs, a run that opens the pass is applied by the loads and
+        // one that closes it by the stores
         std::vector<Ph> phs;
+        std::vector<int> entryp, scatterp;
+        int scatter_at = -1, scatter_end = -1;
         Ph cur;
         const int nops = (int)p.ops.size();
         for (int i = 0; i < nops; ++i) {
@@ -1019,6 +1031,24 @@ struct PassBuilder {
             if (absorb && absorbable(P)) {
                 int j = i;
                 while (j < nops && ops[p.ops[j]].kind != KIND_DIAG && absorbable(ops[p.ops[j]])) ++j;
+                if (gs && i == 0) {
+                    for (int m = i; m < j; ++m) entryp.push_back(p.ops[m]);
+                    cur.begin = j;
+                    i = j - 1;
+                    continue;
+                }
+                // a closing run: only diagonal gates may follow it, and they
+                // must fold into the pass's table through the run (checked
+                // when the ops are emitted)
+                bool closing = gs;
+                for (int m = j; closing && m < nops; ++m) closing = ops[p.ops[m]].kind == KIND_DIAG;
+                if (closing) {
+                    for (int m = i; m < j; ++m) scatterp.push_back(p.ops[m]);
+                    scatter_at = i;
+                    scatter_end = j;
+                    i = nops;
+                    break;
+                }
                 if (j - i >= 2 || cur.need == 0 || j == nops) {
                     cur.end = i;
                     for (int m = i; m < j; ++m) cur.exitp.push_back(p.ops[m]);
@@ -1045,6 +1075,7 @@ struct PassBuilder {
         phs.push_back(cur);
         MERA_RETURN_IF((int)phs.size() > TILE_MAX_PHASES, MERA_EUNSUPPORTED, "tile pass with %zu phases", phs.size());
         A.nph = (int)phs.size();
+        for (int idx : entryp) note_gate(idx);
         std::vector<std::vector<int>> nonreg(A.nph);
         for (int ph = 0; ph < A.nph; ++ph) {
             uint32_t rbm = phs[ph].need;
@@ -1063,8 +1094,19 @@ struct PassBuilder {
             }
             A.ph[ph].op_begin = (int16_t)nop;
             std::vector<int> run;
+            int nop_at_scatter = -1;
             for (int i = phs[ph].begin; i < phs[ph].end; ++i) {
                 const PrepOp& P = ops[p.ops[i]];
+                if (i >= scatter_at && i < scatter_end) {
+                    // the closing run: applied by the stores
+                    if (i == scatter_at) {
+                        MERA_TRY(flush_diag(run));
+                        run.clear();
+                        nop_at_scatter = nop;
+                    }
+                    note_gate(p.ops[i]);
+                    continue;
+                }
                 if (P.kind == KIND_DIAG) {
                     run.push_back(p.ops[i]);
                     continue;
@@ -1075,6 +1117,8 @@ struct PassBuilder {
                 MERA_TRY(add_gate(P, reg_of));
             }
             MERA_TRY(flush_diag(run));
+            MERA_RETURN_IF(nop_at_scatter >= 0 && nop != nop_at_scatter, MERA_EUNSUPPORTED,
+                           "diagonal after the closing permutation did not fold into the table");
             A.ph[ph].op_end = (int16_t)nop;
             for (int idx : phs[ph].exitp) note_gate(idx);
         }
@@ -1088,7 +1132,81 @@ struct PassBuilder {
         };
         A.load_smem = low_reg(0) ? 1 : 0;
         A.store_smem = low_reg(A.nph - 1) ? 1 : 0;
+        // address maps need direct (unstaged) loads / stores
+        MERA_RETURN_IF(!entryp.empty() && A.load_smem, MERA_EUNSUPPORTED, "gathered load needs direct loads");
+        MERA_RETURN_IF(!scatterp.empty() && A.store_smem, MERA_EUNSUPPORTED, "scattered store needs direct stores");
+        if (!entryp.empty()) {
+            Affine f(K);
+            for (int idx : entryp) compose(f, ops[idx]);
+            MERA_RETURN_IF((int)f.w.size() > TILE_MAX_XOFF, MERA_EUNSUPPORTED, "gather with %zu offsets", f.w.size());
+            invert(f);
+            fill_gmap(A.gin, f, nonreg[0], A.ph[0].rb);
+            A.gather = 1;
+        }
+        if (!scatterp.empty()) {
+            Affine f(K);
+            for (int idx : scatterp) compose(f, ops[idx]);
+            MERA_RETURN_IF((int)f.w.size() > TILE_MAX_XOFF, MERA_EUNSUPPORTED, "scatter with %zu offsets", f.w.size());
+            fill_gmap(A.gout, f, nonreg[A.nph - 1], A.ph[A.nph - 1].rb);
+            A.scatter = 1;
+        }
         return build_maps(phs, nonreg);
+    }
+
+    // f <- f^-1 (Gauss-Jordan over GF(2) on the K x K linear part)
+    void invert(Affine& f) const {
+        uint32_t rows[16], inv[16];
+        for (int r = 0; r < K; ++r) {
+            rows[r] = 0;
+            for (int b = 0; b < K; ++b)
+                if ((f.col[b] >> r) & 1u) rows[r] |= 1u << b;
+            inv[r] = 1u << r;
+        }
+        for (int c = 0; c < K; ++c) {
+            int piv = c;
+            while (piv < K && !((rows[piv] >> c) & 1u)) ++piv;
+            std::swap(rows[c], rows[piv]);
+            std::swap(inv[c], inv[piv]);
+            for (int r = 0; r < K; ++r)
+                if (r != c && ((rows[r] >> c) & 1u)) {
+                    rows[r] ^= rows[c];
+                    inv[r] ^= inv[c];
+                }
+        }
+        Affine g(K);
+        for (int b = 0; b < K; ++b) {
+            g.col[b] = 0;
+            for (int r = 0; r < K; ++r)
+                if ((inv[r] >> b) & 1u) g.col[b] |= 1u << r;
+        }
+        auto apply = [&](uint32_t u) {
+            uint32_t v = 0;
+            for (int b = 0; b < K; ++b)
+                if ((u >> b) & 1u) v ^= g.col[b];
+            return v;
+        };
+        g.c = apply(f.c);
+        for (auto& t : f.w) g.w.push_back(std::make_pair(t.first, apply(t.second)));
+        f = g;
+    }
+
+    // local-bit vector -> its global positions
+    unsigned long long to_global(uint32_t u) const {
+        unsigned long long g = 0;
+        for (int b = 0; b < K; ++b)
+            if ((u >> b) & 1u) g |= 1ull << A.tpos[b];
+        return g;
+    }
+    void fill_gmap(GMap& g, const Affine& f, const std::vector<int>& nr, const int8_t* rb) const {
+        memset(&g, 0, sizeof(g));
+        for (size_t t = 0; t < nr.size() && t < 12; ++t) g.tc[t] = to_global(f.col[nr[t]]);
+        for (int r = 0; r < FR; ++r) g.rc[r] = to_global(f.col[rb[r]]);
+        g.c = to_global(f.c);
+        g.nq = (int8_t)f.w.size();
+        for (size_t i = 0; i < f.w.size(); ++i) {
+            g.q[i] = (int8_t)f.w[i].first;
+            g.w[i] = to_global(f.w[i].second);
+        }
     }
 
     void fill_side(XSide& x, const uint32_t* z, const std::vector<int>& nr, const int8_t* rb,

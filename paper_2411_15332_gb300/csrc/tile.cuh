@@ -115,6 +115,19 @@ struct XOut {
     int16_t offv[TILE_MAX_XOFF];
 };
 
+// Global-index map of a load or store with a permutation folded in: the
+// thread's register slot j sits at tile base XOR c XOR (XOR of tc[t] over
+// the set bits t of the thread index) XOR (XOR of rc[r] over the set bits
+// r of j) XOR (XOR of w[i] where the tile's global bit q[i] is set).
+struct GMap {
+    unsigned long long tc[12];
+    unsigned long long rc[FR];
+    unsigned long long c;
+    unsigned long long w[TILE_MAX_XOFF];
+    int8_t q[TILE_MAX_XOFF];
+    int8_t nq;
+};
+
 struct TilePhase {
     int8_t rb[FR];       // local tile bits held in registers, ascending
     int16_t op_begin, op_end;
@@ -149,6 +162,8 @@ struct PassArgs {
     int tpos[16];        // global bit of local bit j, ascending
     XSide ld;            // load staging: slot of element tid + i * 2^(K-FR)
     XSide st;            // store staging: the same for the final copy out
+    int gather, scatter; // 1: phase 0 loads through gin / the last phase stores through gout
+    GMap gin, gout;      // (a permutation at the start / end of the pass rides on the addresses)
     int8_t ntq[TILE_MAX_NT];   // global positions of separable non-tile factors
     TilePhase ph[TILE_MAX_PHASES];
     TileOp ops[TILE_MAX_OPS];
@@ -222,6 +237,24 @@ __device__ __forceinline__ int xbase_out(const XOut& o, uint32_t tid, uint64_t g
     for (int i = 0; i < o.noff; ++i)
         if ((gb >> o.offq[i]) & 1ull) v ^= (int)o.offv[i];
     return v;
+}
+
+__device__ __forceinline__ uint64_t gbase(const GMap& g, uint32_t tid, uint64_t tb) {
+    uint64_t v = tb ^ g.c;
+#pragma unroll
+    for (int t = 0; t < 12; ++t) v ^= (0ull - (uint64_t)((tid >> t) & 1u)) & g.tc[t];
+    for (int i = 0; i < g.nq; ++i)
+        if ((tb >> g.q[i]) & 1ull) v ^= g.w[i];
+    return v;
+}
+template <typename T>
+__device__ __forceinline__ T dep4xl(int j, const T* m) {
+    T r = 0;
+    if (j & 1) r ^= m[0];
+    if (j & 2) r ^= m[1];
+    if (j & 4) r ^= m[2];
+    if (j & 8) r ^= m[3];
+    return r;
 }
 
 // 16-bit mask of this thread's register slots whose controls hold: the
@@ -559,7 +592,7 @@ __device__ __forceinline__ void op_z4(V (&x)[FRA], const TileOp& o, const Z4Term
 // indexed by the local index.  Up to DSEP_SEL_BITS non-tile qubits select
 // one of 2^m pre-multiplied tables (the tile's bits are fixed); beyond that
 // the remaining non-tile factors multiply in per tile.
-constexpr int DSEP_SEL_BITS = 3;
+constexpr int DSEP_SEL_BITS = 5;
 
 template <typename V, int ENG>
 __device__ __forceinline__ void op_dsep(V (&x)[FRA], const TileOp& o, const V* cf, const V* tab, const int8_t* ntq,
@@ -761,7 +794,14 @@ __global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
         const bool read_sm = p > 0 || a.load_smem;
         const int sb = read_sm ? xbase(ph.in, tid) : 0;   // slot maps are XOR-linear: slot = sb ^ xor of sr
         if (p == 0) {
-            if (!a.load_smem) {
+            if (a.gather) {
+                const uint64_t g0 = gbase(a.gin, tid, tb);
+                uint64_t rc[FR];
+#pragma unroll
+                for (int r = 0; r < FR; ++r) rc[r] = a.gin.rc[r];
+#pragma unroll
+                for (int j = 0; j < FRA; ++j) x[j] = raw_load<SV, V>(__ldcs(psi + (g0 ^ dep4xl(j, rc))));
+            } else if (!a.load_smem) {
 #pragma unroll
                 for (int j = 0; j < FRA; ++j) x[j] = raw_load<SV, V>(__ldcs(psi + (gb | dep4(j, gm))));
             } else {
@@ -890,7 +930,14 @@ __global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
                 }
             }
         }
-        if (!a.store_smem) {
+        if (a.scatter) {
+            const uint64_t g0 = gbase(a.gout, tid, tb);
+            uint64_t rc[FR];
+#pragma unroll
+            for (int r = 0; r < FR; ++r) rc[r] = a.gout.rc[r];
+#pragma unroll
+            for (int j = 0; j < FRA; ++j) __stcs(psi + (g0 ^ dep4xl(j, rc)), out[j]);
+        } else if (!a.store_smem) {
 #pragma unroll
             for (int j = 0; j < FRA; ++j) __stcs(psi + (gb | dep4(j, gm)), out[j]);
         } else {
