@@ -1399,6 +1399,7 @@ int fused_build(int n, const std::vector<PrepOp>& ops, FusedPlan<V>& plan, bool 
     }
     // resident segments: runs of tile passes between per-gate ops; the first
     // reads doubles, the last writes doubles
+    plan.dpass.assign(passes.size(), 0);
     if (plan.resident) {
         const size_t np = passes.size();
         for (size_t i = 0; i < np; ++i) {
@@ -1407,6 +1408,17 @@ int fused_build(int n, const std::vector<PrepOp>& ops, FusedPlan<V>& plan, bool 
             A.q_in = (i > 0 && plan.single[i - 1] < 0) ? 1 : 0;
             A.q_out = (i + 1 < np && plan.single[i + 1] < 0) ? 1 : 0;
             A.qgo = A.q_out ? plan.args[i + 1].qgi : A.qgi;
+            // single phase of tables and sign terms between fixed-point
+            // passes: the streaming kernel
+            bool ok = A.nph == 1 && A.q_in && A.q_out && A.qend == 0 && !A.load_smem && !A.store_smem;
+            int ntab = 0, nz = 0;
+            for (int o = A.ph[0].op_begin; ok && o < A.ph[0].op_end; ++o) {
+                const TileOp& op = A.ops[o];
+                if (op.type == TOP_DSEP) ok = ++ntab <= DPASS_MAX_TABS && op.nt <= DSEP_SEL_BITS;
+                else if (op.type == TOP_Z4) ok = ++nz <= 1;
+                else ok = false;
+            }
+            plan.dpass[i] = ok ? 1 : 0;
         }
     }
     return MERA_OK;
@@ -1507,6 +1519,11 @@ int fused_launch(const FusedPlan<V>& plan, size_t i, PassArgs<V>& A, unsigned ny
     MERA_RETURN_IF(tiles > 0x7fffffffull, MERA_EUNSUPPORTED, "too many tiles");
     MERA_RETURN_IF(ny == 0 || ny > 65535, MERA_EUNSUPPORTED, "batch of %u states per launch", ny);
     launch_begin(st, MERA_KCLASS_TILE, 2.0 * (double)(1ull << plan.n) * sizeof(V) * ny);
+    if (sizeof(V) == 16 && plan.dpass[i]) {
+        void* args[] = {&A};
+        MERA_CHECK_CUDA(cudaLaunchKernel(tile_fn_dpass(), dim3((unsigned)tiles, ny), dim3(2u << (K - FR)), args, 0, st));
+        return launch_end(st);
+    }
     MERA_TRY(launch_tile<V>(plan.eng[i], plan.feat[i], dim3((unsigned)tiles, ny), 1u << (K - FR), smem, st, A));
     return launch_end(st);
 }

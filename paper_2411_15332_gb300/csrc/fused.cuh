@@ -16,6 +16,7 @@ struct FusedPlan {
     std::vector<unsigned char> eng, feat;
     std::vector<int> single;              // >= 0: this pass is a per-gate op
     std::vector<V> tabs;                  // diagonal tables to upload (PassArgs::tab)
+    std::vector<unsigned char> dpass;     // 1: single-phase table pass for the streaming kernel
     bool resident = false;                // complex128 state kept as int64 fixed point (ENG_Q)
     int qguard = 0;                       // ENG_Q: headroom bits above the state norm
 };

@@ -930,6 +930,9 @@ __global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
                 }
             }
         }
+        // a permuted load or store moves amplitudes between threads of the
+        // tile in place: every load must precede every store
+        if (a.nph == 1 && (a.gather || a.scatter)) __syncthreads();
         if (a.scatter) {
             const uint64_t g0 = gbase(a.gout, tid, tb);
             uint64_t rc[FR];
@@ -955,6 +958,99 @@ __global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
             const int s0 = xbase(a.st, tid);
 #pragma unroll
             for (int i = 0; i < FRA; ++i) __stcs(psi + (gt | dep4(i, gtop)), sms[s0 ^ dep4x(i, st)]);
+        }
+    }
+}
+
+// ------------------------------------------------ single-phase tables --
+// A resident-engine pass whose only work is one phase of diagonal tables and
+// sign terms (its permutations ride on the gathered loads and scattered
+// stores).  Twice the threads of k_tile, eight amplitudes each (register
+// bit 3 of the pass's phase becomes thread-index bit 8): a smaller register
+// footprint for more resident warps, no shared memory, a compact body.
+// With a permuted load or store every load precedes every store (block
+// barrier), since amplitudes move between threads of the tile in place.
+constexpr int DPASS_MAX_TABS = 2;
+template <int GROUP>
+__global__ void __launch_bounds__(512, 2) k_dpass(const __grid_constant__ PassArgs<double2> a) {
+    constexpr int NA = FRA / 2;   // amplitudes per thread
+    const int K = a.K;
+    const uint32_t tid = threadIdx.x & 255u, hi = threadIdx.x >> 8;
+    const uint64_t tb = insert_zeros(blockIdx.x, a.tpos, K);
+    const TilePhase& ph = a.ph[0];
+    uint64_t gm[FR], rin[FR], rout[FR];
+    int lm[FR];
+#pragma unroll
+    for (int r = 0; r < FR; ++r) {
+        gm[r] = 1ull << a.tpos[ph.rb[r]];
+        lm[r] = 1 << ph.rb[r];
+        rin[r] = a.gin.rc[r];
+        rout[r] = a.gout.rc[r];
+    }
+    const uint32_t lb = insert_reg_zeros(tid, ph.rb) | (hi ? (uint32_t)lm[FR - 1] : 0u);
+    const uint64_t gb = tb | spread_bits(lb, a.tpos, K);
+    const uint64_t gi0 = a.gather ? (gbase(a.gin, tid, tb) ^ (hi ? rin[FR - 1] : 0ull)) : 0ull;
+    const uint64_t go0 = a.scatter ? (gbase(a.gout, tid, tb) ^ (hi ? rout[FR - 1] : 0ull)) : 0ull;
+    // the pass's tables (selection applied) and sign-term range
+    const int4* tabs[DPASS_MAX_TABS];
+    int ntab = 0, z0 = 0, z1 = 0;
+    for (int o = ph.op_begin; o < ph.op_end; ++o) {
+        const TileOp& op = a.ops[o];
+        if (op.type == TOP_DSEP && ntab < DPASS_MAX_TABS) {
+            uint32_t sel = 0;
+            for (int f = 0; f < op.nt; ++f) sel |= (uint32_t)((gb >> a.ntq[op.aux2 + f]) & 1ull) << f;
+            tabs[ntab++] = reinterpret_cast<const int4*>(a.tab) + op.aux + ((size_t)sel << K);
+        } else if (op.type == TOP_Z4) {
+            z0 = op.aux;
+            z1 = op.aux + op.aux2;
+        }
+    }
+    I2 x[NA];
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+        const uint64_t gi = a.gather ? (gi0 ^ dep4xl(j, rin)) : (gb | dep4(j, gm));
+        const longlong2 v = __ldcs(reinterpret_cast<const longlong2*>(a.psi + gi));
+        x[j].x = v.x;
+        x[j].y = v.y;
+    }
+    if (a.gather || a.scatter) __syncthreads();
+    const int k = a.q_out ? a.qgo - a.qgi : 0;   // change to the next pass's format
+    const long long half = k > 0 ? (1ll << (k - 1)) : 0ll;
+#pragma unroll
+    for (int g = 0; g < NA; g += GROUP) {
+        for (int t = 0; t < ntab; ++t) {
+            int4 d[GROUP];
+#pragma unroll
+            for (int u = 0; u < GROUP; ++u) d[u] = __ldg(tabs[t] + (lb | dep4(g + u, lm)));
+#pragma unroll
+            for (int u = 0; u < GROUP; ++u) x[g + u] = qcmul(d[u], x[g + u]);
+        }
+        if (z1 > z0) {
+            int e[GROUP];
+#pragma unroll
+            for (int u = 0; u < GROUP; ++u) e[u] = 0;
+            for (int z = z0; z < z1; ++z) {
+                const Z4Term tz = a.z4[z];
+#pragma unroll
+                for (int u = 0; u < GROUP; ++u)
+                    if (((gb | dep4(g + u, gm)) & tz.mask) == tz.vals) e[u] += tz.e;
+            }
+#pragma unroll
+            for (int u = 0; u < GROUP; ++u) x[g + u] = mul_ik(x[g + u], e[u] & 3);
+        }
+#pragma unroll
+        for (int u = 0; u < GROUP; ++u) {
+            long long vx = x[g + u].x, vy = x[g + u].y;
+            if (k > 0) {
+                vx = (vx + half) >> k;
+                vy = (vy + half) >> k;
+            } else if (k < 0) {
+                vx = (long long)((unsigned long long)vx << (-k));
+                vy = (long long)((unsigned long long)vy << (-k));
+            }
+            const int j = g + u;
+            const uint64_t go = a.scatter ? (go0 ^ dep4xl(j, rout)) : (gb | dep4(j, gm));
+            __stcs(reinterpret_cast<longlong2*>(a.psi + go), make_longlong2(vx, vy));
         }
     }
 }

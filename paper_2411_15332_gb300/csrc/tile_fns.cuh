@@ -9,6 +9,8 @@ namespace mera {
 // complex128 kernels by engine and feature set; qin = 1 selects the
 // fixed-point variant that converts its input from doubles
 const void* tile_fn_q(int feat, int qin);
+// the streaming kernel of single-phase table passes (resident engine)
+const void* tile_fn_dpass();
 const void* tile_fn_i64(int feat, int qin);
 const void* tile_fn_fp(int feat, int qin);
 // the complex64 kernel

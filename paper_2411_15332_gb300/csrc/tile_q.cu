@@ -4,6 +4,8 @@
 
 namespace mera {
 
+const void* tile_fn_dpass() { return (const void*)k_dpass<4>; }
+
 const void* tile_fn_q(int feat, int qin) {
     if (qin) {
         switch (feat) {

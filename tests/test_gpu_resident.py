@@ -80,3 +80,24 @@ def test_unnormalised_state(scale):
     s.close()
     ref = sv.simulate(n, ops, psi0=psi)
     assert max_err(got, ref) <= 1e-12 * scale
+
+
+def test_permutations_on_loads_and_stores_in_place():
+    """Rotations, then CNOT ladders and rotations about Z only: the ladders
+    ride on gathered loads and scattered stores of single-phase passes that
+    move amplitudes between threads of a tile in place (every load must
+    precede every store).  Checked against the oracle amplitude by
+    amplitude."""
+    n = 20
+    rng = np.random.default_rng(21)
+    ops = [op("RY", (q,), (), (float(rng.uniform(0, 6.28)),)) for q in range(n)]
+    for _ in range(6):
+        ops += [op("X", (q + 1,), (q,)) for q in range(n - 1)]
+        ops += [op("RZ", (q,), (), (float(rng.uniform(0, 6.28)),)) for q in range(n)]
+        ops += [op("X", (q,), (q + 1,)) for q in range(n - 2, -1, -1)]
+    s = new_state(n)
+    s.apply_circuit(ops, mode="fused")
+    got = s.to_numpy()
+    s.close()
+    ref = sv.simulate(n, ops)
+    assert max_err(got, ref) <= 1e-13
