@@ -1328,6 +1328,87 @@ int launch_tile<float2>(int, int, dim3 grid, unsigned block, size_t smem, cudaSt
 // Build every pass of a circuit: kernel arguments (without state pointers),
 // engine and kernel variant per pass, and the diagonal tables.  Passes with
 // `single` >= 0 are per-gate ops (returned in `singles`, -1 otherwise).
+// Arguments of the streaming kernel from a single-phase pass (K = 12,
+// n <= 32): per thread-index bit and register bit the global index masks
+// of the load, the store and the natural positions, and the local masks.
+// Thread bits 0..7 are the phase's non-register bits, thread bit 8 its top
+// register bit; register bits 0..2 its lower register bits.
+template <typename V>
+static void dpass_args(const PassArgs<V>& A, int n, DPassArgs& d) {
+    memset(&d, 0, sizeof(d));
+    d.K = A.K;
+    const int K = A.K;
+    const TilePhase& ph = A.ph[0];
+    bool reg[16] = {false};
+    for (int r = 0; r < FR; ++r) reg[ph.rb[r]] = true;
+    int nr[16], nnr = 0;
+    for (int b = 0; b < K; ++b)
+        if (!reg[b]) nr[nnr++] = b;
+    // tile index -> non-tile positions (ascending), as runs
+    bool tilebit[64] = {false};
+    for (int b = 0; b < K; ++b) tilebit[A.tpos[b]] = true;
+    int src = 0;
+    for (int q = 0; q < n;) {
+        if (tilebit[q]) {
+            ++q;
+            continue;
+        }
+        int w = 0;
+        while (q + w < n && !tilebit[q + w]) ++w;
+        d.run_src[d.nruns] = (uint32_t)src;
+        d.run_w[d.nruns] = (uint32_t)w;
+        d.run_dst[d.nruns] = (uint32_t)q;
+        ++d.nruns;
+        src += w;
+        q += w;
+    }
+    auto g32 = [&](int local) { return (uint32_t)1u << A.tpos[local]; };
+    for (int t = 0; t < 8; ++t) {
+        d.nat.t[t] = g32(nr[t]);
+        d.tloc[t] = 1u << nr[t];
+    }
+    d.nat.t[8] = g32(ph.rb[3]);
+    d.tloc[8] = 1u << ph.rb[3];
+    for (int r = 0; r < 3; ++r) {
+        d.nat.r[r] = g32(ph.rb[r]);
+        d.rloc[r] = 1u << ph.rb[r];
+    }
+    auto from_g = [&](const GMap& g, DMap& m) {
+        for (int t = 0; t < 8; ++t) m.t[t] = (uint32_t)g.tc[t];
+        m.t[8] = (uint32_t)g.rc[3];
+        for (int r = 0; r < 3; ++r) m.r[r] = (uint32_t)g.rc[r];
+        m.c = (uint32_t)g.c;
+        m.nq = g.nq;
+        for (int i = 0; i < g.nq; ++i) {
+            m.q[i] = g.q[i];
+            m.w[i] = (uint32_t)g.w[i];
+        }
+    };
+    d.in = d.nat;
+    d.out = d.nat;
+    if (A.gather) from_g(A.gin, d.in);
+    if (A.scatter) from_g(A.gout, d.out);
+    d.permuted = (A.gather || A.scatter) ? 1 : 0;
+    for (int o = ph.op_begin; o < ph.op_end; ++o) {
+        const TileOp& op = A.ops[o];
+        if (op.type == TOP_DSEP) {
+            d.tab_off[d.ntab] = op.aux;
+            d.tab_nt[d.ntab] = op.nt;
+            for (int f = 0; f < op.nt; ++f) d.tab_q[d.ntab][f] = A.ntq[op.aux2 + f];
+            ++d.ntab;
+        } else if (op.type == TOP_Z4) {
+            for (int z = 0; z < op.aux2; ++z) {
+                const Z4Term& t = A.z4[op.aux + z];
+                d.z4[d.nz].mask = (uint32_t)t.mask;
+                d.z4[d.nz].vals = (uint32_t)t.vals;
+                d.z4[d.nz].e = t.e;
+                ++d.nz;
+            }
+        }
+    }
+    d.shift = A.q_out ? A.qgo - A.qgi : 0;
+}
+
 template <typename V>
 int fused_build(int n, const std::vector<PrepOp>& ops, FusedPlan<V>& plan, bool fp_only, bool resident_ok) {
     plan.K = fused_tile_bits(sizeof(V) == 16 ? MERA_C128 : MERA_C64, n);
@@ -1400,6 +1481,7 @@ int fused_build(int n, const std::vector<PrepOp>& ops, FusedPlan<V>& plan, bool 
     // resident segments: runs of tile passes between per-gate ops; the first
     // reads doubles, the last writes doubles
     plan.dpass.assign(passes.size(), 0);
+    plan.dargs.assign(plan.resident ? passes.size() : 0, DPassArgs());
     if (plan.resident) {
         const size_t np = passes.size();
         for (size_t i = 0; i < np; ++i) {
@@ -1409,8 +1491,9 @@ int fused_build(int n, const std::vector<PrepOp>& ops, FusedPlan<V>& plan, bool 
             A.q_out = (i + 1 < np && plan.single[i + 1] < 0) ? 1 : 0;
             A.qgo = A.q_out ? plan.args[i + 1].qgi : A.qgi;
             // single phase of tables and sign terms between fixed-point
-            // passes: the streaming kernel
-            bool ok = A.nph == 1 && A.q_in && A.q_out && A.qend == 0 && !A.load_smem && !A.store_smem;
+            // passes of a state of at most 2^32 amplitudes: the streaming kernel
+            bool ok = A.nph == 1 && A.q_in && A.q_out && A.qend == 0 && !A.load_smem && !A.store_smem && n <= 32 &&
+                      plan.K == 12;
             int ntab = 0, nz = 0;
             for (int o = A.ph[0].op_begin; ok && o < A.ph[0].op_end; ++o) {
                 const TileOp& op = A.ops[o];
@@ -1419,6 +1502,7 @@ int fused_build(int n, const std::vector<PrepOp>& ops, FusedPlan<V>& plan, bool 
                 else ok = false;
             }
             plan.dpass[i] = ok ? 1 : 0;
+            if (ok) dpass_args(A, n, plan.dargs[i]);
         }
     }
     return MERA_OK;
@@ -1519,9 +1603,12 @@ int fused_launch(const FusedPlan<V>& plan, size_t i, PassArgs<V>& A, unsigned ny
     MERA_RETURN_IF(tiles > 0x7fffffffull, MERA_EUNSUPPORTED, "too many tiles");
     MERA_RETURN_IF(ny == 0 || ny > 65535, MERA_EUNSUPPORTED, "batch of %u states per launch", ny);
     launch_begin(st, MERA_KCLASS_TILE, 2.0 * (double)(1ull << plan.n) * sizeof(V) * ny);
-    if (sizeof(V) == 16 && plan.dpass[i]) {
-        void* args[] = {&A};
-        MERA_CHECK_CUDA(cudaLaunchKernel(tile_fn_dpass(), dim3((unsigned)tiles, ny), dim3(2u << (K - FR)), args, 0, st));
+    if (sizeof(V) == 16 && ny == 1 && plan.dpass[i]) {
+        DPassArgs d = plan.dargs[i];
+        d.psi = reinterpret_cast<double2*>(A.psi);
+        d.tab = reinterpret_cast<const int4*>(A.tab);
+        void* args[] = {&d};
+        MERA_CHECK_CUDA(cudaLaunchKernel(tile_fn_dpass(), dim3((unsigned)tiles, 1), dim3(2u << (K - FR)), args, 0, st));
         return launch_end(st);
     }
     MERA_TRY(launch_tile<V>(plan.eng[i], plan.feat[i], dim3((unsigned)tiles, ny), 1u << (K - FR), smem, st, A));

@@ -17,6 +17,7 @@ struct FusedPlan {
     std::vector<int> single;              // >= 0: this pass is a per-gate op
     std::vector<V> tabs;                  // diagonal tables to upload (PassArgs::tab)
     std::vector<unsigned char> dpass;     // 1: single-phase table pass for the streaming kernel
+    std::vector<DPassArgs> dargs;         // its arguments (state / table pointers set at launch)
     bool resident = false;                // complex128 state kept as int64 fixed point (ENG_Q)
     int qguard = 0;                       // ENG_Q: headroom bits above the state norm
 };

@@ -965,75 +965,113 @@ __global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
 // ------------------------------------------------ single-phase tables --
 // A resident-engine pass whose only work is one phase of diagonal tables and
 // sign terms (its permutations ride on the gathered loads and scattered
-// stores).  Twice the threads of k_tile, eight amplitudes each (register
-// bit 3 of the pass's phase becomes thread-index bit 8): a smaller register
-// footprint for more resident warps, no shared memory, a compact body.
-// With a permuted load or store every load precedes every store (block
-// barrier), since amplitudes move between threads of the tile in place.
+// stores) on a state of at most 2^32 amplitudes.  512 threads per tile,
+// eight amplitudes each; every address is an XOR of masks the host
+// precomputes per thread-index bit and register bit (32-bit arithmetic), so
+// a thread's setup is a few XORs and an access is one XOR and one address
+// add.  No shared memory; with a permuted load or store every load precedes
+// every store (block barrier), since amplitudes move between threads of the
+// tile in place.
 constexpr int DPASS_MAX_TABS = 2;
-template <int GROUP>
-__global__ void __launch_bounds__(512, 2) k_dpass(const __grid_constant__ PassArgs<double2> a) {
-    constexpr int NA = FRA / 2;   // amplitudes per thread
-    const int K = a.K;
-    const uint32_t tid = threadIdx.x & 255u, hi = threadIdx.x >> 8;
-    const uint64_t tb = insert_zeros(blockIdx.x, a.tpos, K);
-    const TilePhase& ph = a.ph[0];
-    uint64_t gm[FR], rin[FR], rout[FR];
-    int lm[FR];
+constexpr int DPASS_TBITS = 9;     // thread-index bits (512 threads)
+constexpr int DPASS_RBITS = 3;     // register bits (8 amplitudes)
+struct DMap {                      // global index = tile base ^ c ^ thread part ^ register part ^ tile terms
+    uint32_t t[DPASS_TBITS];
+    uint32_t r[DPASS_RBITS];
+    uint32_t c;
+    uint32_t w[TILE_MAX_XOFF];
+    int8_t q[TILE_MAX_XOFF];
+    int8_t nq;
+};
+struct DZ4 {
+    uint32_t mask, vals;
+    int e;
+};
+struct DPassArgs {
+    double2* psi;
+    const int4* tab;
+    int K;
+    int nruns;                     // tile index -> tile base: runs of non-tile positions
+    uint32_t run_src[12], run_w[12], run_dst[12];
+    DMap in, out, nat;             // load map, store map, natural (unpermuted) positions
+    uint32_t tloc[DPASS_TBITS], rloc[DPASS_RBITS];   // local index (table offset)
+    int ntab;
+    int tab_off[DPASS_MAX_TABS], tab_nt[DPASS_MAX_TABS];
+    int8_t tab_q[DPASS_MAX_TABS][8];
+    int shift;                     // right shift into the next pass's format (negative: left)
+    int permuted;                  // 1: the load or the store map is a permutation
+    int nz;
+    DZ4 z4[TILE_MAX_Z4];
+};
+
+__device__ __forceinline__ uint32_t dbase(const DMap& m, uint32_t tid, uint32_t tb) {
+    uint32_t v = tb ^ m.c;
 #pragma unroll
-    for (int r = 0; r < FR; ++r) {
-        gm[r] = 1ull << a.tpos[ph.rb[r]];
-        lm[r] = 1 << ph.rb[r];
-        rin[r] = a.gin.rc[r];
-        rout[r] = a.gout.rc[r];
+    for (int t = 0; t < DPASS_TBITS; ++t) v ^= (0u - ((tid >> t) & 1u)) & m.t[t];
+    for (int i = 0; i < m.nq; ++i)
+        if ((tb >> m.q[i]) & 1u) v ^= m.w[i];
+    return v;
+}
+__device__ __forceinline__ uint32_t dreg(int j, const uint32_t* r) {
+    uint32_t v = 0;
+    if (j & 1) v ^= r[0];
+    if (j & 2) v ^= r[1];
+    if (j & 4) v ^= r[2];
+    return v;
+}
+
+template <int GROUP>
+__global__ void __launch_bounds__(512, 2) k_dpass(const __grid_constant__ DPassArgs a) {
+    constexpr int NA = 1 << DPASS_RBITS;
+    const uint32_t tid = threadIdx.x;
+    uint32_t tb = 0;
+    for (int i = 0; i < a.nruns; ++i) tb |= ((blockIdx.x >> a.run_src[i]) & ((1u << a.run_w[i]) - 1u)) << a.run_dst[i];
+    const uint32_t gi0 = dbase(a.in, tid, tb), go0 = dbase(a.out, tid, tb), gn0 = dbase(a.nat, tid, tb);
+    uint32_t lb = 0;
+#pragma unroll
+    for (int t = 0; t < DPASS_TBITS; ++t) lb ^= (0u - ((tid >> t) & 1u)) & a.tloc[t];
+    uint32_t rin[DPASS_RBITS], rout[DPASS_RBITS], rnat[DPASS_RBITS], rloc[DPASS_RBITS];
+#pragma unroll
+    for (int r = 0; r < DPASS_RBITS; ++r) {
+        rin[r] = a.in.r[r];
+        rout[r] = a.out.r[r];
+        rnat[r] = a.nat.r[r];
+        rloc[r] = a.rloc[r];
     }
-    const uint32_t lb = insert_reg_zeros(tid, ph.rb) | (hi ? (uint32_t)lm[FR - 1] : 0u);
-    const uint64_t gb = tb | spread_bits(lb, a.tpos, K);
-    const uint64_t gi0 = a.gather ? (gbase(a.gin, tid, tb) ^ (hi ? rin[FR - 1] : 0ull)) : 0ull;
-    const uint64_t go0 = a.scatter ? (gbase(a.gout, tid, tb) ^ (hi ? rout[FR - 1] : 0ull)) : 0ull;
-    // the pass's tables (selection applied) and sign-term range
     const int4* tabs[DPASS_MAX_TABS];
-    int ntab = 0, z0 = 0, z1 = 0;
-    for (int o = ph.op_begin; o < ph.op_end; ++o) {
-        const TileOp& op = a.ops[o];
-        if (op.type == TOP_DSEP && ntab < DPASS_MAX_TABS) {
-            uint32_t sel = 0;
-            for (int f = 0; f < op.nt; ++f) sel |= (uint32_t)((gb >> a.ntq[op.aux2 + f]) & 1ull) << f;
-            tabs[ntab++] = reinterpret_cast<const int4*>(a.tab) + op.aux + ((size_t)sel << K);
-        } else if (op.type == TOP_Z4) {
-            z0 = op.aux;
-            z1 = op.aux + op.aux2;
-        }
+    for (int t = 0; t < a.ntab; ++t) {
+        uint32_t sel = 0;
+        for (int f = 0; f < a.tab_nt[t]; ++f) sel |= ((tb >> a.tab_q[t][f]) & 1u) << f;
+        tabs[t] = a.tab + a.tab_off[t] + ((size_t)sel << a.K);
     }
     I2 x[NA];
 #pragma unroll
     for (int j = 0; j < NA; ++j) {
-        const uint64_t gi = a.gather ? (gi0 ^ dep4xl(j, rin)) : (gb | dep4(j, gm));
-        const longlong2 v = __ldcs(reinterpret_cast<const longlong2*>(a.psi + gi));
+        const longlong2 v = __ldcs(reinterpret_cast<const longlong2*>(a.psi + (gi0 ^ dreg(j, rin))));
         x[j].x = v.x;
         x[j].y = v.y;
     }
-    if (a.gather || a.scatter) __syncthreads();
-    const int k = a.q_out ? a.qgo - a.qgi : 0;   // change to the next pass's format
+    if (a.permuted) __syncthreads();
+    const int k = a.shift;
     const long long half = k > 0 ? (1ll << (k - 1)) : 0ll;
 #pragma unroll
     for (int g = 0; g < NA; g += GROUP) {
-        for (int t = 0; t < ntab; ++t) {
+        for (int t = 0; t < a.ntab; ++t) {
             int4 d[GROUP];
 #pragma unroll
-            for (int u = 0; u < GROUP; ++u) d[u] = __ldg(tabs[t] + (lb | dep4(g + u, lm)));
+            for (int u = 0; u < GROUP; ++u) d[u] = __ldg(tabs[t] + (lb ^ dreg(g + u, rloc)));
 #pragma unroll
             for (int u = 0; u < GROUP; ++u) x[g + u] = qcmul(d[u], x[g + u]);
         }
-        if (z1 > z0) {
+        if (a.nz) {
             int e[GROUP];
 #pragma unroll
             for (int u = 0; u < GROUP; ++u) e[u] = 0;
-            for (int z = z0; z < z1; ++z) {
-                const Z4Term tz = a.z4[z];
+            for (int z = 0; z < a.nz; ++z) {
+                const DZ4 tz = a.z4[z];
 #pragma unroll
                 for (int u = 0; u < GROUP; ++u)
-                    if (((gb | dep4(g + u, gm)) & tz.mask) == tz.vals) e[u] += tz.e;
+                    if (((gn0 ^ dreg(g + u, rnat)) & tz.mask) == tz.vals) e[u] += tz.e;
             }
 #pragma unroll
             for (int u = 0; u < GROUP; ++u) x[g + u] = mul_ik(x[g + u], e[u] & 3);
@@ -1048,9 +1086,7 @@ __global__ void __launch_bounds__(512, 2) k_dpass(const __grid_constant__ PassAr
                 vx = (long long)((unsigned long long)vx << (-k));
                 vy = (long long)((unsigned long long)vy << (-k));
             }
-            const int j = g + u;
-            const uint64_t go = a.scatter ? (go0 ^ dep4xl(j, rout)) : (gb | dep4(j, gm));
-            __stcs(reinterpret_cast<longlong2*>(a.psi + go), make_longlong2(vx, vy));
+            __stcs(reinterpret_cast<longlong2*>(a.psi + (go0 ^ dreg(g + u, rout))), make_longlong2(vx, vy));
         }
     }
 }
