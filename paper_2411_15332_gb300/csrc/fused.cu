@@ -447,6 +447,18 @@ struct PassBuilder {
         return MERA_OK;
     }
 
+    // An identity separable table op, open for later diagonal runs.
+    int open_empty_table() {
+        TileOp* o;
+        MERA_TRY(add_op(&o));
+        o->type = TOP_DSEP;
+        ot = OpenTable();
+        ot.open = true;
+        ot.opi = (int)(o - A.ops);
+        ot.runs.push_back(Run{{}, {}, {}});
+        return write_table();
+    }
+
     int add_op(TileOp** out) {
         MERA_RETURN_IF(nop >= TILE_MAX_OPS, MERA_EUNSUPPORTED, "tile pass op table full");
         *out = &A.ops[nop++];
@@ -1102,6 +1114,9 @@ struct PassBuilder {
                     if (i == scatter_at) {
                         MERA_TRY(flush_diag(run));
                         run.clear();
+                        // diagonals after the run fold, through it, into a
+                        // table applied before it: open one if none is
+                        if (!ot.open && scatter_end < phs[ph].end) MERA_TRY(open_empty_table());
                         nop_at_scatter = nop;
                     }
                     note_gate(p.ops[i]);
