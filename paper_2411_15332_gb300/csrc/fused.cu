@@ -1049,15 +1049,21 @@ struct PassBuilder {
                     i = j - 1;
                     continue;
                 }
-                // a closing run: only diagonal gates may follow it, and they
-                // must fold into the pass's table through the run (checked
-                // when the ops are emitted)
+                // a closing region: from here on only absorbable permutations
+                // and diagonal gates; the permutations are applied by the
+                // stores, the diagonals must fold into the pass's table
+                // through them, or be sign terms after the last of them
+                // (checked when the ops are emitted)
                 bool closing = gs;
-                for (int m = j; closing && m < nops; ++m) closing = ops[p.ops[m]].kind == KIND_DIAG;
+                for (int m = i; closing && m < nops; ++m) {
+                    const PrepOp& Q = ops[p.ops[m]];
+                    closing = Q.kind == KIND_DIAG || absorbable(Q);
+                }
                 if (closing) {
-                    for (int m = i; m < j; ++m) scatterp.push_back(p.ops[m]);
+                    for (int m = i; m < nops; ++m)
+                        if (ops[p.ops[m]].kind != KIND_DIAG) scatterp.push_back(p.ops[m]);
                     scatter_at = i;
-                    scatter_end = j;
+                    scatter_end = nops;
                     i = nops;
                     break;
                 }
@@ -1109,16 +1115,20 @@ struct PassBuilder {
             int nop_at_scatter = -1;
             for (int i = phs[ph].begin; i < phs[ph].end; ++i) {
                 const PrepOp& P = ops[p.ops[i]];
-                if (i >= scatter_at && i < scatter_end) {
-                    // the closing run: applied by the stores
+                if (scatter_at >= 0 && i >= scatter_at && P.kind != KIND_DIAG) {
+                    // a permutation of the closing region: applied by the stores
+                    MERA_TRY(flush_diag(run));
+                    run.clear();
                     if (i == scatter_at) {
-                        MERA_TRY(flush_diag(run));
-                        run.clear();
-                        // diagonals after the run fold, through it, into a
-                        // table applied before it: open one if none is
-                        if (!ot.open && scatter_end < phs[ph].end) MERA_TRY(open_empty_table());
+                        // diagonals after it fold, through it, into a table
+                        // applied before it: open one if none is
+                        bool later = false;
+                        for (int m = i + 1; m < phs[ph].end; ++m) later = later || ops[p.ops[m]].kind == KIND_DIAG;
+                        if (!ot.open && later) MERA_TRY(open_empty_table());
                         nop_at_scatter = nop;
                     }
+                    MERA_RETURN_IF(nop != nop_at_scatter, MERA_EUNSUPPORTED,
+                                   "diagonal between closing permutations did not fold into the table");
                     note_gate(p.ops[i]);
                     continue;
                 }
@@ -1132,8 +1142,13 @@ struct PassBuilder {
                 MERA_TRY(add_gate(P, reg_of));
             }
             MERA_TRY(flush_diag(run));
-            MERA_RETURN_IF(nop_at_scatter >= 0 && nop != nop_at_scatter, MERA_EUNSUPPORTED,
-                           "diagonal after the closing permutation did not fold into the table");
+            // after the closing run only sign terms may remain: they apply at
+            // the scattered (permuted) index
+            for (int o = nop_at_scatter; nop_at_scatter >= 0 && o < nop; ++o) {
+                MERA_RETURN_IF(A.ops[o].type != TOP_Z4, MERA_EUNSUPPORTED,
+                               "diagonal after the closing permutation did not fold into the table");
+                A.ops[o].c = 2;
+            }
             A.ph[ph].op_end = (int16_t)nop;
             for (int idx : phs[ph].exitp) note_gate(idx);
         }
@@ -1417,6 +1432,7 @@ static void dpass_args(const PassArgs<V>& A, int n, DPassArgs& d) {
                 d.z4[d.nz].mask = (uint32_t)t.mask;
                 d.z4[d.nz].vals = (uint32_t)t.vals;
                 d.z4[d.nz].e = t.e;
+                d.z4[d.nz].post = op.c == 2 ? 1 : 0;
                 ++d.nz;
             }
         }

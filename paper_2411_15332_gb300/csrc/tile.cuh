@@ -75,7 +75,8 @@ enum TileOpType : int8_t {
 
 struct TileOp {
     int8_t type;
-    int8_t a, b, c;      // register bits (a is the most significant sub-index bit); c: 1 = per-state coefficients
+    int8_t a, b, c;      // register bits (a is the most significant sub-index bit); c: 1 = per-state
+                         // coefficients; sign terms: 2 = matched on the scattered store index
     int8_t nt;           // diag: number of targets; dsep: non-tile factors
     int8_t tq[3];        // diag: global target positions (tq[0] most significant)
     int32_t coef;        // first coefficient in PassArgs::coef
@@ -841,7 +842,23 @@ __global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
         }
         for (int o = ph.op_begin; o < ph.op_end; ++o) {
             const TileOp& op = a.ops[o];
-            const V* cf = (op.c ? bcf : reinterpret_cast<const V*>(a.coef)) + op.coef;
+            if (op.type == TOP_Z4 && op.c == 2) {
+                // sign terms after the closing permutation: on the store index
+                const uint64_t g0 = gbase(a.gout, tid, tb);
+                int e[FRA];
+#pragma unroll
+                for (int j = 0; j < FRA; ++j) e[j] = 0;
+                for (int t = 0; t < op.aux2; ++t) {
+                    const Z4Term z = a.z4[op.aux + t];
+#pragma unroll
+                    for (int j = 0; j < FRA; ++j)
+                        if (((g0 ^ dep4xl(j, a.gout.rc)) & z.mask) == z.vals) e[j] += z.e;
+                }
+#pragma unroll
+                for (int j = 0; j < FRA; ++j) x[j] = mul_ik(x[j], e[j] & 3);
+                continue;
+            }
+            const V* cf = (op.c == 1 ? bcf : reinterpret_cast<const V*>(a.coef)) + op.coef;
             apply_tile_op<V, SV, ENG, FEAT>(x, op, a, cf, gb, gm, lb, lm);
         }
         // exit slots: the same as the entry slots unless the exchange
@@ -985,7 +1002,8 @@ struct DMap {                      // global index = tile base ^ c ^ thread part
 };
 struct DZ4 {
     uint32_t mask, vals;
-    int e;
+    int16_t e;
+    int16_t post;                  // 1: matched on the stored (permuted) index
 };
 struct DPassArgs {
     double2* psi;
@@ -1070,8 +1088,10 @@ __global__ void __launch_bounds__(512, 2) k_dpass(const __grid_constant__ DPassA
             for (int z = 0; z < a.nz; ++z) {
                 const DZ4 tz = a.z4[z];
 #pragma unroll
-                for (int u = 0; u < GROUP; ++u)
-                    if (((gn0 ^ dreg(g + u, rnat)) & tz.mask) == tz.vals) e[u] += tz.e;
+                for (int u = 0; u < GROUP; ++u) {
+                    const uint32_t gi = tz.post ? (go0 ^ dreg(g + u, rout)) : (gn0 ^ dreg(g + u, rnat));
+                    if ((gi & tz.mask) == tz.vals) e[u] += tz.e;
+                }
             }
 #pragma unroll
             for (int u = 0; u < GROUP; ++u) x[g + u] = mul_ik(x[g + u], e[u] & 3);
