@@ -1806,6 +1806,10 @@ static int describe_fused(int n, int dtype, const std::vector<PrepOp>& ops, std:
         std::string dsep;
         for (int o = 0; o < nop; ++o)
             if (A.ops[o].type == TOP_DSEP) dsep += " dsep_nontile=" + std::to_string((int)A.ops[o].nt);
+        int nterms = 0;
+        for (int o = 0; o < nop; ++o)
+            if (A.ops[o].type == TOP_Z4) nterms += A.ops[o].aux2;
+        dsep += " z4_terms=" + std::to_string(nterms) + (plan.dpass[i] ? " stream" : "");
         dsep += " phase_ops=[";
         for (int ph = 0; ph < A.nph; ++ph)
             dsep += std::to_string(A.ph[ph].op_end - A.ph[ph].op_begin) + (A.ph[ph].permuted ? "p" : "") +

@@ -401,21 +401,26 @@ __device__ __forceinline__ long long qlow(int a, int b) { return (long long)(__u
 __device__ __forceinline__ long long qcombine(long long m1, long long m2) {
     return 2 * m1 + ((m2 + (1ll << 29)) >> 30);
 }
+// x * c / 2^61 for |x| < 2^60 and a Q61 value c with |c| < 2^61.5, both
+// split into 31-bit limbs, rounded to nearest
+__device__ __forceinline__ long long qmul_q(long long x, int ch, int cl) {
+    int h, l;
+    qsplit(x, h, l);
+    return qcombine((long long)h * ch, (long long)h * cl + (long long)l * ch + qlow(l, cl));
+}
+// Complex product with three real products (c + id)(a + ib):
+// k1 = c (a + b), k2 = a (d - c), k3 = b (c + d); re = k1 - k3, im = k1 + k2
+// (each k rounded to nearest: error <= 1 unit per part, unbiased, 0 stays 0).
 __device__ __forceinline__ I2 qcmul(int4 d, I2 x) {
-    int rh, rl, ih, il;
-    qsplit(x.x, rh, rl);
-    qsplit(x.y, ih, il);
+    const long long c = ((long long)d.x << 31) + (long long)(unsigned)d.y;
+    const long long e = ((long long)d.z << 31) + (long long)(unsigned)d.w;
+    const long long dmc = e - c, cpd = c + e;
+    const long long k1 = qmul_q(x.x + x.y, d.x, d.y);
+    const long long k2 = qmul_q(x.x, (int)(dmc >> 31), (int)((unsigned)dmc & 0x7FFFFFFFu));
+    const long long k3 = qmul_q(x.y, (int)(cpd >> 31), (int)((unsigned)cpd & 0x7FFFFFFFu));
     I2 r;
-    // re = xr dr - xi di
-    long long m1 = (long long)rh * d.x - (long long)ih * d.z;
-    long long m2 = (long long)rh * d.y + (long long)rl * d.x - (long long)ih * d.w - (long long)il * d.z +
-                   qlow(rl, d.y) - qlow(il, d.w);
-    r.x = qcombine(m1, m2);
-    // im = xr di + xi dr
-    m1 = (long long)rh * d.z + (long long)ih * d.x;
-    m2 = (long long)rh * d.w + (long long)rl * d.z + (long long)ih * d.y + (long long)il * d.x + qlow(rl, d.w) +
-         qlow(il, d.y);
-    r.y = qcombine(m1, m2);
+    r.x = k1 - k3;
+    r.y = k1 + k2;
     return r;
 }
 // x * c for a real Q61 constant c = ch * 2^31 + cl
