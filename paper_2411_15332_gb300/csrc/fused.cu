@@ -1374,23 +1374,28 @@ static void dpass_args(const PassArgs<V>& A, int n, DPassArgs& d) {
     int nr[16], nnr = 0;
     for (int b = 0; b < K; ++b)
         if (!reg[b]) nr[nnr++] = b;
-    // tile index -> non-tile positions (ascending), as runs
-    bool tilebit[64] = {false};
+    // tile index -> non-tile positions, as runs.  The qubits that select a
+    // table slice take the most significant tile-index bits: the tiles a SM
+    // runs one after another (block indices a grid-width apart) then read
+    // the same 64 KiB slice, which stays in L1.
+    bool tilebit[64] = {false}, selbit[64] = {false};
     for (int b = 0; b < K; ++b) tilebit[A.tpos[b]] = true;
-    int src = 0;
-    for (int q = 0; q < n;) {
-        if (tilebit[q]) {
-            ++q;
-            continue;
-        }
-        int w = 0;
-        while (q + w < n && !tilebit[q + w]) ++w;
-        d.run_src[d.nruns] = (uint32_t)src;
+    for (int o = ph.op_begin; o < ph.op_end; ++o)
+        if (A.ops[o].type == TOP_DSEP)
+            for (int f = 0; f < A.ops[o].nt; ++f) selbit[A.ntq[A.ops[o].aux2 + f]] = true;
+    int order[64], norder = 0;
+    for (int q = 0; q < n; ++q)
+        if (!tilebit[q] && !selbit[q]) order[norder++] = q;
+    for (int q = 0; q < n; ++q)
+        if (!tilebit[q] && selbit[q]) order[norder++] = q;
+    for (int i = 0; i < norder;) {
+        int w = 1;
+        while (i + w < norder && order[i + w] == order[i] + w) ++w;
+        d.run_src[d.nruns] = (uint32_t)i;
         d.run_w[d.nruns] = (uint32_t)w;
-        d.run_dst[d.nruns] = (uint32_t)q;
+        d.run_dst[d.nruns] = (uint32_t)order[i];
         ++d.nruns;
-        src += w;
-        q += w;
+        i += w;
     }
     auto g32 = [&](int local) { return (uint32_t)1u << A.tpos[local]; };
     for (int t = 0; t < 8; ++t) {

@@ -1015,7 +1015,7 @@ struct DPassArgs {
     const int4* tab;
     int K;
     int nruns;                     // tile index -> tile base: runs of non-tile positions
-    uint32_t run_src[12], run_w[12], run_dst[12];
+    uint32_t run_src[32], run_w[32], run_dst[32];
     DMap in, out, nat;             // load map, store map, natural (unpermuted) positions
     uint32_t tloc[DPASS_TBITS], rloc[DPASS_RBITS];   // local index (table offset)
     int ntab;
