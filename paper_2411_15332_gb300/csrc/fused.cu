@@ -1643,8 +1643,13 @@ int fused_launch(const FusedPlan<V>& plan, size_t i, PassArgs<V>& A, unsigned ny
         DPassArgs d = plan.dargs[i];
         d.psi = reinterpret_cast<double2*>(A.psi);
         d.tab = reinterpret_cast<const int4*>(A.tab);
+        d.ntiles = (uint32_t)tiles;
+        // a few tiles per CTA: the thread's address setup is shared
+        static int sms = 0;
+        if (!sms) MERA_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0));
+        const uint64_t ctas = std::max<uint64_t>(1, std::min<uint64_t>(tiles, 16ull * (uint64_t)sms));
         void* args[] = {&d};
-        MERA_CHECK_CUDA(cudaLaunchKernel(tile_fn_dpass(), dim3((unsigned)tiles, 1), dim3(2u << (K - FR)), args, 0, st));
+        MERA_CHECK_CUDA(cudaLaunchKernel(tile_fn_dpass(), dim3((unsigned)ctas, 1), dim3(2u << (K - FR)), args, 0, st));
         return launch_end(st);
     }
     MERA_TRY(launch_tile<V>(plan.eng[i], plan.feat[i], dim3((unsigned)tiles, ny), 1u << (K - FR), smem, st, A));

@@ -1023,6 +1023,7 @@ struct DPassArgs {
     int8_t tab_q[DPASS_MAX_TABS][8];
     int shift;                     // right shift into the next pass's format (negative: left)
     int permuted;                  // 1: the load or the store map is a permutation
+    uint32_t ntiles;               // tiles of the pass (the grid may be smaller)
     int nz;
     DZ4 z4[TILE_MAX_Z4];
 };
@@ -1047,9 +1048,8 @@ template <int GROUP>
 __global__ void __launch_bounds__(512, 2) k_dpass(const __grid_constant__ DPassArgs a) {
     constexpr int NA = 1 << DPASS_RBITS;
     const uint32_t tid = threadIdx.x;
-    uint32_t tb = 0;
-    for (int i = 0; i < a.nruns; ++i) tb |= ((blockIdx.x >> a.run_src[i]) & ((1u << a.run_w[i]) - 1u)) << a.run_dst[i];
-    const uint32_t gi0 = dbase(a.in, tid, tb), go0 = dbase(a.out, tid, tb), gn0 = dbase(a.nat, tid, tb);
+    // the thread's parts of the maps are the same in every tile
+    const uint32_t ti = dbase(a.in, tid, 0), to = dbase(a.out, tid, 0), tn = dbase(a.nat, tid, 0);
     uint32_t lb = 0;
 #pragma unroll
     for (int t = 0; t < DPASS_TBITS; ++t) lb ^= (0u - ((tid >> t) & 1u)) & a.tloc[t];
@@ -1061,6 +1061,16 @@ __global__ void __launch_bounds__(512, 2) k_dpass(const __grid_constant__ DPassA
         rnat[r] = a.nat.r[r];
         rloc[r] = a.rloc[r];
     }
+    // several tiles per CTA (grid-stride), each as in a one-tile launch
+    for (uint32_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+    uint32_t tb = 0;
+    for (int i = 0; i < a.nruns; ++i) tb |= ((tile >> a.run_src[i]) & ((1u << a.run_w[i]) - 1u)) << a.run_dst[i];
+    uint32_t gi0 = tb ^ ti, go0 = tb ^ to;
+    const uint32_t gn0 = tb ^ tn;
+    for (int i = 0; i < a.in.nq; ++i)
+        if ((tb >> a.in.q[i]) & 1u) gi0 ^= a.in.w[i];
+    for (int i = 0; i < a.out.nq; ++i)
+        if ((tb >> a.out.q[i]) & 1u) go0 ^= a.out.w[i];
     const int4* tabs[DPASS_MAX_TABS];
     for (int t = 0; t < a.ntab; ++t) {
         uint32_t sel = 0;
@@ -1114,6 +1124,7 @@ __global__ void __launch_bounds__(512, 2) k_dpass(const __grid_constant__ DPassA
             __stcs(reinterpret_cast<longlong2*>(a.psi + (go0 ^ dreg(g + u, rout))), make_longlong2(vx, vy));
         }
     }
+    }   // tiles (disjoint index sets: no ordering between them is needed)
 }
 
 }  // namespace mera
