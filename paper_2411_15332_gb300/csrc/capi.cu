@@ -247,6 +247,7 @@ int mera_state_destroy(mera_state* s) {
     if (s->prog) cudaFree(s->prog);
     if (s->prog_host) cudaFreeHost(s->prog_host);
     fused_cache_free(s);
+    if (s->pong) cudaFree(s->pong);
     delete s;
     return MERA_OK;
     API_END

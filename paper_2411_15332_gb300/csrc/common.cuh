@@ -77,6 +77,11 @@ struct mera_state {
     // last fused circuit: its key (the raw ops) and its built passes, whose
     // diagonal tables are resident in `prog`
     void* fused_cache = nullptr;
+    // second state-sized buffer: resident fixed-point runs alternate between
+    // it and `data` (out-of-place passes), ending in `data`
+    void* pong = nullptr;
+    size_t pong_bytes = 0;
+    bool pong_failed = false;
 };
 
 namespace mera {

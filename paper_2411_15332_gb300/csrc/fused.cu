@@ -1642,6 +1642,7 @@ int fused_launch(const FusedPlan<V>& plan, size_t i, PassArgs<V>& A, unsigned ny
     if (sizeof(V) == 16 && ny == 1 && plan.dpass[i]) {
         DPassArgs d = plan.dargs[i];
         d.psi = reinterpret_cast<double2*>(A.psi);
+        d.psi_out = reinterpret_cast<double2*>(A.psi_out ? A.psi_out : A.psi);
         d.tab = reinterpret_cast<const int4*>(A.tab);
         d.ntiles = (uint32_t)tiles;
         // a few tiles per CTA: the thread's address setup is shared
@@ -1711,13 +1712,49 @@ static int launch_plan(mera_state* s, FusedPlan<V>& plan, const std::vector<Prep
         const int* qS = reinterpret_cast<const int*>(reinterpret_cast<char*>(s->scratch) + 8192);
         for (PassArgs<V>& A : plan.args) A.qS = qS;
     }
-    for (size_t i = 0; i < plan.args.size(); ++i) {
+    // resident runs alternate between the state and a second buffer (passes
+    // out of place need no load-before-store ordering); the buffers are
+    // assigned so that every run ends in the state
+    void* other = nullptr;
+    if (plan.resident && !s->pong_failed) {
+        const size_t bytes = num_amps(s) * elem_bytes(s->dtype);
+        if (s->pong_bytes < bytes) {
+            if (s->pong) {
+                MERA_CHECK_CUDA(cudaStreamSynchronize(s->stream));
+                cudaFree(s->pong);
+            }
+            s->pong = nullptr;
+            s->pong_bytes = 0;
+            if (cudaMalloc(&s->pong, bytes) == cudaSuccess) {
+                s->pong_bytes = bytes;
+            } else {
+                cudaGetLastError();
+                s->pong_failed = true;   // in place from now on
+            }
+        }
+        other = s->pong;
+    }
+    const size_t np = plan.args.size();
+    for (size_t i = 0; i < np;) {
         if (plan.single[i] >= 0) {
             MERA_TRY(apply_prepared(s, ops[plan.single[i]]));
+            ++i;
             continue;
         }
-        plan.args[i].psi = reinterpret_cast<V*>(s->data);
-        MERA_TRY(fused_launch<V>(plan, i, plan.args[i], 1, s->stream));
+        size_t e = i;   // the run of tile passes [i, e)
+        while (e < np && plan.single[e] < 0) ++e;
+        V* bufs[2] = {reinterpret_cast<V*>(s->data), reinterpret_cast<V*>(other)};
+        int cur = 0;    // buffer holding the input
+        for (size_t k = i; k < e; ++k) {
+            PassArgs<V>& A = plan.args[k];
+            // pass k writes buffer (e - 1 - k) % 2 of {state, other}
+            const int dst = other ? (int)((e - 1 - k) % 2) : 0;
+            A.psi = bufs[cur];
+            A.psi_out = dst == cur ? nullptr : bufs[dst];
+            MERA_TRY(fused_launch<V>(plan, k, A, 1, s->stream));
+            cur = dst;
+        }
+        i = e;
     }
     return MERA_OK;
 }

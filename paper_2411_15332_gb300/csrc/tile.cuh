@@ -141,6 +141,7 @@ struct TilePhase {
 template <typename V>
 struct PassArgs {
     V* psi;
+    V* psi_out;          // null: in place; else the pass writes here (same layout)
     const V* tab;        // separable-diagonal tables (device), 2^K entries each
     // batches of states (blockIdx.y): state = psi + slot * bstride with
     // slot = slots[blockIdx.y] (or blockIdx.y when slots is NULL); ops with
@@ -765,6 +766,7 @@ __global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
     const uint64_t tile = blockIdx.x;
     const uint64_t tb = insert_zeros(tile, a.tpos, K);    // global index of local 0
     SV* const psi = a.psi + (a.slots ? (unsigned long long)a.slots[blockIdx.y] : (unsigned long long)blockIdx.y) * a.bstride;
+    SV* const pso = a.psi_out ? a.psi_out : psi;   // (out of place only for single-state launches)
     const V* const bcf = reinterpret_cast<const V*>(a.bcoef) + (size_t)blockIdx.y * a.bcstride;
     V x[FRA];
     int S = 0;   // ENG_I64 / ENG_Q: fixed-point exponent
@@ -954,17 +956,17 @@ __global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
         }
         // a permuted load or store moves amplitudes between threads of the
         // tile in place: every load must precede every store
-        if (a.nph == 1 && (a.gather || a.scatter)) __syncthreads();
+        if (a.nph == 1 && (a.gather || a.scatter) && !a.psi_out) __syncthreads();
         if (a.scatter) {
             const uint64_t g0 = gbase(a.gout, tid, tb);
             uint64_t rc[FR];
 #pragma unroll
             for (int r = 0; r < FR; ++r) rc[r] = a.gout.rc[r];
 #pragma unroll
-            for (int j = 0; j < FRA; ++j) __stcs(psi + (g0 ^ dep4xl(j, rc)), out[j]);
+            for (int j = 0; j < FRA; ++j) __stcs(pso + (g0 ^ dep4xl(j, rc)), out[j]);
         } else if (!a.store_smem) {
 #pragma unroll
-            for (int j = 0; j < FRA; ++j) __stcs(psi + (gb | dep4(j, gm)), out[j]);
+            for (int j = 0; j < FRA; ++j) __stcs(pso + (gb | dep4(j, gm)), out[j]);
         } else {
             // unpermuted: a thread rewrites only the slots it read itself
 #pragma unroll
@@ -979,7 +981,7 @@ __global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
             for (int r = 0; r < FR; ++r) st[r] = a.st.rc[r];
             const int s0 = xbase(a.st, tid);
 #pragma unroll
-            for (int i = 0; i < FRA; ++i) __stcs(psi + (gt | dep4(i, gtop)), sms[s0 ^ dep4x(i, st)]);
+            for (int i = 0; i < FRA; ++i) __stcs(pso + (gt | dep4(i, gtop)), sms[s0 ^ dep4x(i, st)]);
         }
     }
 }
@@ -1012,6 +1014,7 @@ struct DZ4 {
 };
 struct DPassArgs {
     double2* psi;
+    double2* psi_out;              // the pass writes here (may equal psi)
     const int4* tab;
     int K;
     int nruns;                     // tile index -> tile base: runs of non-tile positions
@@ -1084,7 +1087,7 @@ __global__ void __launch_bounds__(512, 2) k_dpass(const __grid_constant__ DPassA
         x[j].x = v.x;
         x[j].y = v.y;
     }
-    if (a.permuted) __syncthreads();
+    if (a.permuted && a.psi_out == a.psi) __syncthreads();
     const int k = a.shift;
     const long long half = k > 0 ? (1ll << (k - 1)) : 0ll;
 #pragma unroll
@@ -1121,7 +1124,7 @@ __global__ void __launch_bounds__(512, 2) k_dpass(const __grid_constant__ DPassA
                 vx = (long long)((unsigned long long)vx << (-k));
                 vy = (long long)((unsigned long long)vy << (-k));
             }
-            __stcs(reinterpret_cast<longlong2*>(a.psi + (go0 ^ dreg(g + u, rout))), make_longlong2(vx, vy));
+            __stcs(reinterpret_cast<longlong2*>(a.psi_out + (go0 ^ dreg(g + u, rout))), make_longlong2(vx, vy));
         }
     }
     }   // tiles (disjoint index sets: no ordering between them is needed)

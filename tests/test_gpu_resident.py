@@ -101,3 +101,26 @@ def test_permutations_on_loads_and_stores_in_place():
     s.close()
     ref = sv.simulate(n, ops)
     assert max_err(got, ref) <= 1e-13
+
+
+@pytest.mark.parametrize("layers", [2, 3])
+def test_runs_split_by_per_gate_ops(layers):
+    """A three-target gate runs as a per-gate kernel between two runs of
+    fixed-point passes; each run alternates between the state and a second
+    buffer and must end in the state (odd and even pass counts)."""
+    n = 16
+    rng = np.random.default_rng(30 + layers)
+    ops = [op("RY", (q,), (), (float(rng.uniform(0, 6.28)),)) for q in range(n)]
+    body = inputs.layered_circuit(n, layers, seed=31)[n:]
+    half = len(body) // 2
+    perm8 = np.roll(np.eye(8, dtype=np.complex128), 1, axis=0)   # a three-qubit permutation
+    first = ops + body[:half]
+    second = body[half:]
+    s = new_state(n)
+    s.apply_circuit(first + [(perm8, (9, 2, 13), (), (), 0)] + second, mode="fused")
+    got = s.to_numpy()
+    s.close()
+    ref = sv.simulate(n, first)
+    ref = sv.apply_matrix(ref, n, perm8, (9, 2, 13))
+    ref = sv.simulate(n, second, psi0=ref)
+    assert max_err(got, ref) <= 1e-13
