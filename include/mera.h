@@ -229,7 +229,8 @@ int mera_observables_noalloc(const void* dev_psi, int n, int dtype, int q, void*
  *       same row (or the row start), bit 63 marks the last non-zero of its
  *       row.  Rows in order; every row needs at least one non-zero.
  * nq <= 32 (indices need 2 nq bits).  `stream` is a cudaStream_t (NULL =
- * legacy default); calls are asynchronous on it except *_export/*_info.
+ * legacy default); calls are asynchronous on it except the export and info
+ * calls.
  * Objects are owned by the caller and freed with *_destroy. */
 typedef struct mera_dax mera_dax;
 typedef struct mera_das mera_das;

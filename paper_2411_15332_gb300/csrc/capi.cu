@@ -336,16 +336,12 @@ int mera_apply_gate(mera_state* s, int gate, const int* targets, int nt, const i
     for (int j = 0; j < nt; ++j) op.targets[j] = targets[j];
     MERA_TRY(to_mask(controls, nc, s->n, &op.cmask));
     op.cvals = op.cmask;
-    int k = 0;
-    cplx tmp[64];
     if (gate != MERA_GATE_MATRIX && gate >= 0 && gate < MERA_GATE_COUNT) {
         // copy exactly the parameters the gate takes
         static const int npar[MERA_GATE_COUNT] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 2, 2, 4,
                                                   0, 0, 0, 0, 1, 1, 1, 1, 0, 0};
         MERA_RETURN_IF(npar[gate] > 0 && params == nullptr, MERA_EINVAL, "gate %d needs params", gate);
         for (int j = 0; j < npar[gate]; ++j) op.params[j] = params[j];
-        (void)k;
-        (void)tmp;
     }
     PrepOp P;
     MERA_TRY(prepare_op(op, s->n, &P));

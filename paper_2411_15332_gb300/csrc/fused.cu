@@ -198,7 +198,6 @@ static void plan_segment(const std::vector<PrepOp>& ops, std::vector<int> remain
         uint64_t ph_need = 0;
         int nph = 1;
         int nh = 0;
-        bool inexact = false;
         std::vector<int> deferred;
         for (int idx : remaining) {
             const PrepOp& P = ops[idx];
@@ -232,13 +231,11 @@ static void plan_segment(const std::vector<PrepOp>& ops, std::vector<int> remain
                 ++nops;
                 ncoef += coef_need(P);
                 if (P.is_h) ++nh;
-                if (!op_is_exact(P)) inexact = true;
             } else {
                 deferred.push_back(idx);
                 blocked |= q;
             }
         }
-        (void)inexact;
         // fill the remaining tile bits with the lowest free positions
         for (int b = 0; b < n && popc(p.tile_mask) < K; ++b) p.tile_mask |= 1ull << b;
         passes.push_back(std::move(p));
@@ -678,7 +675,7 @@ struct PassBuilder {
         MERA_TRY(add_op(&o));
         o->cmask = P.cmask;
         o->cvals = P.cvals;
-        int rr[3];
+        int rr[3] = {0, 0, 0};
         for (int t = 0; t < P.k; ++t) rr[t] = reg_of[local_of[P.t[t]]];
         if (P.k == 1) {
             o->a = (int8_t)rr[0];
@@ -1034,7 +1031,7 @@ struct PassBuilder {
         // one that closes it by the stores
         std::vector<Ph> phs;
         std::vector<int> entryp, scatterp;
-        int scatter_at = -1, scatter_end = -1;
+        int scatter_at = -1;
         Ph cur;
         const int nops = (int)p.ops.size();
         for (int i = 0; i < nops; ++i) {
@@ -1063,7 +1060,6 @@ struct PassBuilder {
                     for (int m = i; m < nops; ++m)
                         if (ops[p.ops[m]].kind != KIND_DIAG) scatterp.push_back(p.ops[m]);
                     scatter_at = i;
-                    scatter_end = nops;
                     i = nops;
                     break;
                 }

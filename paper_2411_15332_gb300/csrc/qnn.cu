@@ -306,8 +306,6 @@ __global__ void k_adj_finish(const double* __restrict__ partial, int nrows, int 
 }
 
 // ------------------------------------------------------------- host side --
-static int batch_elem(const mera_batch* b) { return (int)elem_bytes(b->dtype); }
-
 static int upload_slots(mera_batch* b, const int* slots, int nslots, int offset) {
     MERA_RETURN_IF(nslots < 1 || nslots > b->cap, MERA_EINVAL, "%d slots for a batch of %d", nslots, b->cap);
     std::vector<int> tmp(nslots);

@@ -755,7 +755,6 @@ __global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
                                                         (ENG != ENG_I64 && FEAT == (FEAT_GATES | FEAT_DIAG)))) ? 2 : 1)
     k_tile(const __grid_constant__ PassArgs<SV> a) {
     using V = typename std::conditional<ENG == ENG_FP, SV, I2>::type;
-    constexpr int EB = sizeof(SV);
     extern __shared__ __align__(16) unsigned char smraw[];
     SV* sms = reinterpret_cast<SV*>(smraw);     // staging of stored values
     V* sm = reinterpret_cast<V*>(smraw);        // exchange between phases
