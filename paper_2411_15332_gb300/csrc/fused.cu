@@ -1014,9 +1014,13 @@ struct PassBuilder {
         // permutation runs at the ends of the pass on the load / store
         // addresses, the others on exchanges; then exchanges only; then
         // register ops (too many phases or exchange offsets)
-        int r = build_phases_with(p, true, true);
-        if (r == MERA_OK) return r;
-        restore();
+        // (load / store address maps exist in the resident engine only)
+        int r = MERA_EUNSUPPORTED;
+        if (engine == ENG_Q) {
+            r = build_phases_with(p, true, true);
+            if (r == MERA_OK) return r;
+            restore();
+        }
         r = build_phases_with(p, true, false);
         if (r == MERA_OK) return r;
         restore();

@@ -801,7 +801,7 @@ __global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
         const bool read_sm = p > 0 || a.load_smem;
         const int sb = read_sm ? xbase(ph.in, tid) : 0;   // slot maps are XOR-linear: slot = sb ^ xor of sr
         if (p == 0) {
-            if (a.gather) {
+            if (ENG == ENG_Q && a.gather) {
                 const uint64_t g0 = gbase(a.gin, tid, tb);
                 uint64_t rc[FR];
 #pragma unroll
@@ -848,6 +848,7 @@ __global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
         }
         for (int o = ph.op_begin; o < ph.op_end; ++o) {
             const TileOp& op = a.ops[o];
+            if constexpr (ENG == ENG_Q) {
             if (op.type == TOP_Z4 && op.c == 2) {
                 // sign terms after the closing permutation: on the store index
                 const uint64_t g0 = gbase(a.gout, tid, tb);
@@ -863,6 +864,7 @@ __global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
 #pragma unroll
                 for (int j = 0; j < FRA; ++j) x[j] = mul_ik(x[j], e[j] & 3);
                 continue;
+            }
             }
             const V* cf = (op.c == 1 ? bcf : reinterpret_cast<const V*>(a.coef)) + op.coef;
             apply_tile_op<V, SV, ENG, FEAT>(x, op, a, cf, gb, gm, lb, lm);
@@ -955,8 +957,8 @@ __global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
         }
         // a permuted load or store moves amplitudes between threads of the
         // tile in place: every load must precede every store
-        if (a.nph == 1 && (a.gather || a.scatter) && !a.psi_out) __syncthreads();
-        if (a.scatter) {
+        if (ENG == ENG_Q && a.nph == 1 && (a.gather || a.scatter) && !a.psi_out) __syncthreads();
+        if (ENG == ENG_Q && a.scatter) {
             const uint64_t g0 = gbase(a.gout, tid, tb);
             uint64_t rc[FR];
 #pragma unroll
