@@ -1120,11 +1120,16 @@ struct PassBuilder {
                     MERA_TRY(flush_diag(run));
                     run.clear();
                     if (i == scatter_at) {
-                        // diagonals after it fold, through it, into a table
-                        // applied before it: open one if none is
-                        bool later = false;
-                        for (int m = i + 1; m < phs[ph].end; ++m) later = later || ops[p.ops[m]].kind == KIND_DIAG;
-                        if (!ot.open && later) MERA_TRY(open_empty_table());
+                        // diagonals with general phases after it fold,
+                        // through it, into a table applied before it: open
+                        // one if none is (exact sign patterns need none:
+                        // they apply at the scattered index)
+                        bool general = false;
+                        for (int m = i + 1; m < phs[ph].end; ++m) {
+                            const PrepOp& Q = ops[p.ops[m]];
+                            general = general || (Q.kind == KIND_DIAG && !op_is_exact(Q));
+                        }
+                        if (!ot.open && general) MERA_TRY(open_empty_table());
                         nop_at_scatter = nop;
                     }
                     MERA_RETURN_IF(nop != nop_at_scatter, MERA_EUNSUPPORTED,
