@@ -17,6 +17,7 @@
 #include <cstdlib>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -320,6 +321,7 @@ struct PassBuilder {
     int engine = ENG_FP;
     bool fp_only = false;   // keep every pass in the float engine
     bool qres = false;      // resident fixed point: every pass in ENG_Q
+    bool stage_load = false;  // stage the first load through shared memory (pipelined kernel)
 
     // The open separable-diagonal op: later diagonal runs fold into its
     // table while only pure index permutations (X, CNOT, SWAP, Toffoli:
@@ -1165,7 +1167,7 @@ struct PassBuilder {
                 if (A.ph[ph].rb[r] < S) return true;
             return false;
         };
-        A.load_smem = low_reg(0) ? 1 : 0;
+        A.load_smem = (stage_load || low_reg(0)) ? 1 : 0;
         A.store_smem = low_reg(A.nph - 1) ? 1 : 0;
         // address maps need direct (unstaged) loads / stores
         MERA_RETURN_IF(!entryp.empty() && A.load_smem, MERA_EUNSUPPORTED, "gathered load needs direct loads");
@@ -1450,6 +1452,23 @@ static void dpass_args(const PassArgs<V>& A, int n, DPassArgs& d) {
     d.shift = A.q_out ? A.qgo - A.qgi : 0;
 }
 
+// A complex128 int64-engine pass of butterflies and sign terms only, without
+// gathered loads or scattered stores: the pipelined Hadamard-pass kernel.
+template <typename V>
+static bool hpass_ok(const PassArgs<V>& A, int eng, int K) {
+    if (sizeof(V) != 16 || (eng != ENG_I64 && eng != ENG_Q)) return false;
+    if (A.gather || A.scatter || A.nph > HP_MAXPH || (1 << (K - FR)) > HP_THREADS) return false;
+    for (int p = 0; p < A.nph; ++p)
+        if (A.ph[p].out.noff != 0) return false;   // no tile-dependent exit offsets
+    if (((size_t)1 << K) * sizeof(V) > 64 * 1024) return false;
+    for (int p = 0; p < A.nph; ++p)
+        for (int o = A.ph[p].op_begin; o < A.ph[p].op_end; ++o) {
+            const TileOp& op = A.ops[o];
+            if (!(op.type == TOP_H || (op.type == TOP_Z4 && op.c == 0))) return false;
+        }
+    return true;
+}
+
 template <typename V>
 int fused_build(int n, const std::vector<PrepOp>& ops, FusedPlan<V>& plan, bool fp_only, bool resident_ok) {
     plan.K = fused_tile_bits(sizeof(V) == 16 ? MERA_C128 : MERA_C64, n);
@@ -1462,17 +1481,23 @@ int fused_build(int n, const std::vector<PrepOp>& ops, FusedPlan<V>& plan, bool 
     plan.eng.assign(passes.size(), 0);
     plan.feat.assign(passes.size(), 0);
     plan.single.assign(passes.size(), -1);
+    plan.hpass.assign(passes.size(), 0);
     plan.tabs.clear();
     // resident fixed point: complex128, unitary gates only (the norm bounds
     // every amplitude), and some arithmetic to gain from it
     plan.resident = false;
     plan.qguard = 0;
+    plan.dither = false;
+    bool mixed = false;
     if (sizeof(V) == 16 && !fp_only && resident_ok) {
-        // unitary gates only (the norm bounds every amplitude), some
-        // arithmetic, and every mixing (non-monomial) gate before the first
-        // monomial one: the monomial body keeps each amplitude's magnitude,
-        // so the global scale costs it no precision and nothing later
-        // concentrates rounding errors
+        // unitary gates only (the norm bounds every amplitude) and some
+        // arithmetic.  Where every mixing (non-monomial) gate precedes the
+        // first monomial one, the monomial body keeps each amplitude's
+        // magnitude, so the global scale costs it no precision and nothing
+        // later concentrates rounding errors.  Otherwise (Hadamard layers
+        // between sign flips, as in Grover) only if every tile pass runs the
+        // Hadamard-pass kernel, whose dithered rounding keeps the errors of
+        // equal amplitudes uncorrelated (checked after the passes are built)
         bool unit = true, arith = false, body = false, mixed_after = false;
         for (const PrepOp& P : ops) {
             if (P.kind == KIND_IDENTITY) continue;
@@ -1485,17 +1510,34 @@ int fused_build(int n, const std::vector<PrepOp>& ops, FusedPlan<V>& plan, bool 
             if (monomial) body = true;
             else if (body) mixed_after = true;
         }
-        plan.resident = unit && arith && !mixed_after;
+        plan.resident = unit && arith;
+        mixed = mixed_after;
     }
     for (size_t i = 0; i < passes.size(); ++i) {
         if (passes[i].single >= 0) {
             plan.single[i] = passes[i].single;
             continue;
         }
-        PassBuilder<V> b(plan.args[i], plan.tabs, ops, plan.K, n);
-        b.fp_only = fp_only;
-        b.qres = plan.resident;
-        MERA_TRY(b.build(passes[i], sizeof(V) == 16));
+        const size_t ntab0 = plan.tabs.size();
+        auto make = [&](bool stage) {
+            std::unique_ptr<PassBuilder<V>> r(new PassBuilder<V>(plan.args[i], plan.tabs, ops, plan.K, n));
+            r->fp_only = fp_only;
+            r->qres = plan.resident;
+            r->stage_load = stage;
+            return r;
+        };
+        std::unique_ptr<PassBuilder<V>> bp = make(false);
+        MERA_TRY(bp->build(passes[i], sizeof(V) == 16));
+        // Hadamard / sign-term passes of the int64 engines run in the
+        // pipelined kernel, which reads every tile through the load staging
+        if (hpass_ok(plan.args[i], bp->engine, plan.K) && !plan.args[i].load_smem) {
+            plan.tabs.resize(ntab0);
+            bp = make(true);
+            MERA_TRY(bp->build(passes[i], sizeof(V) == 16));
+            MERA_RETURN_IF(!hpass_ok(plan.args[i], bp->engine, plan.K) || !plan.args[i].load_smem,
+                           MERA_EUNSUPPORTED, "staged rebuild of a Hadamard pass changed its form");
+        }
+        PassBuilder<V>& b = *bp;
         plan.eng[i] = (unsigned char)b.engine;
         if (plan.eng[i] == ENG_Q) {
             // Headroom over the state norm: unnormalised butterflies grow an
@@ -1518,6 +1560,35 @@ int fused_build(int n, const std::vector<PrepOp>& ops, FusedPlan<V>& plan, bool 
             plan.qguard = std::max(plan.qguard, A.qgi);
         }
         plan.feat[i] = (unsigned char)round_feat(plan.eng[i], b.features(), sizeof(V) == 16);
+        plan.hpass[i] = hpass_ok(plan.args[i], plan.eng[i], plan.K) ? 1 : 0;
+    }
+    if (plan.resident && mixed)
+        for (size_t i = 0; i < passes.size(); ++i)
+            if (plan.single[i] < 0 && !plan.hpass[i]) return fused_build(n, ops, plan, fp_only, false);
+    plan.dither = plan.resident && mixed;
+    if (plan.dither) {
+        // Every tile pass runs the Hadamard-pass kernel: one rounding per
+        // pass (no scaling at phase exits; headroom for all the pass's
+        // levels), and an odd level count leaves a factor sqrt(2) on the
+        // stored state (value * 2^(S - g) * sqrt(2)^p) for the next pass to
+        // take, so only a run's last pass may multiply by 1/sqrt(2)
+        plan.qguard = 0;
+        int pend = 0;
+        for (size_t i = 0; i < passes.size(); ++i) {
+            if (plan.single[i] >= 0) {
+                pend = 0;
+                continue;
+            }
+            PassArgs<V>& A = plan.args[i];
+            const bool last = i + 1 == passes.size() || plan.single[i + 1] >= 0;
+            for (int ph = 0; ph < A.nph; ++ph) A.ph[ph].qsh = 0;
+            const int tot = A.nh + pend;
+            const int pout = last ? 0 : (tot & 1);
+            A.qend = tot - pout;
+            A.qgi = (tot + 1) / 2 + 2;
+            plan.qguard = std::max(plan.qguard, A.qgi);
+            pend = pout;
+        }
     }
     // resident segments: runs of tile passes between per-gate ops; the first
     // reads doubles, the last writes doubles
@@ -1656,6 +1727,38 @@ int fused_launch(const FusedPlan<V>& plan, size_t i, PassArgs<V>& A, unsigned ny
         const uint64_t ctas = std::max<uint64_t>(1, std::min<uint64_t>(tiles, 16ull * (uint64_t)sms));
         void* args[] = {&d};
         MERA_CHECK_CUDA(cudaLaunchKernel(tile_fn_dpass(), dim3((unsigned)ctas, 1), dim3(2u << (K - FR)), args, 0, st));
+        return launch_end(st);
+    }
+    if (sizeof(V) == 16 && ny == 1 && plan.hpass[i]) {
+        static int sms = 0;
+        if (!sms) MERA_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0));
+        const unsigned ctas =
+            (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(tiles, (uint64_t)HP_CTAS_PER_SM * (uint64_t)sms));
+        HPassArgs h;
+        uint64_t tilemask = 0;
+        for (int b = 0; b < K; ++b) tilemask |= 1ull << A.tpos[b];
+        h.ntmask = (plan.n >= 64 ? ~0ull : ((1ull << plan.n) - 1ull)) & ~tilemask;
+        h.dstride = 0;
+        uint64_t g = ctas;
+        for (int q = 0; q < 64 && g; ++q)
+            if ((h.ntmask >> q) & 1ull) {
+                if (g & 1ull) h.dstride |= 1ull << q;
+                g >>= 1;
+            }
+        h.ntiles = (unsigned)tiles;
+        h.salt = 0x9E3779B9u * (uint32_t)(i + 1) ^ 0x7F4A7C15u;
+        h.dither = plan.dither ? 1 : 0;
+        for (int ph = 0; ph < A.nph; ++ph)
+            for (int r = 0; r < FR; ++r) h.gm[ph][r] = 1ull << A.tpos[A.ph[ph].rb[r]];
+        const void* fn = tile_fn_hpass(plan.eng[i], plan.eng[i] == ENG_Q && !A.q_in ? 1 : 0);
+        const size_t hsm = ((size_t)1 << K) * sizeof(V);
+        static std::vector<std::pair<const void*, size_t>> opted;
+        if (std::find(opted.begin(), opted.end(), std::make_pair(fn, hsm)) == opted.end()) {
+            MERA_CHECK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm));
+            opted.push_back(std::make_pair(fn, hsm));
+        }
+        void* args[] = {reinterpret_cast<void*>(&A), &h};
+        MERA_CHECK_CUDA(cudaLaunchKernel(fn, dim3(ctas), dim3(1u << (K - FR)), args, hsm, st));
         return launch_end(st);
     }
     MERA_TRY(launch_tile<V>(plan.eng[i], plan.feat[i], dim3((unsigned)tiles, ny), 1u << (K - FR), smem, st, A));
@@ -1838,8 +1941,8 @@ static int describe_fused(int n, int dtype, const std::vector<PrepOp>& ops, std:
     MERA_TRY(fused_build<V>(n, ops, plan, false, true));
     const int K = plan.K;
     char line[640];
-    snprintf(line, sizeof(line), "K=%d L=%d passes=%zu resident=%d qguard=%d table_bytes=%zu\n", K,
-             low_bits_for(dtype, K), plan.args.size(), plan.resident ? 1 : 0, plan.qguard,
+    snprintf(line, sizeof(line), "K=%d L=%d passes=%zu resident=%d dither=%d qguard=%d table_bytes=%zu\n", K,
+             low_bits_for(dtype, K), plan.args.size(), plan.resident ? 1 : 0, plan.dither ? 1 : 0, plan.qguard,
              plan.tabs.size() * sizeof(V));
     *out += line;
     static const char* eng_name[3] = {"fp", "i64", "q"};
@@ -1861,7 +1964,8 @@ static int describe_fused(int n, int dtype, const std::vector<PrepOp>& ops, std:
         int nterms = 0;
         for (int o = 0; o < nop; ++o)
             if (A.ops[o].type == TOP_Z4) nterms += A.ops[o].aux2;
-        dsep += " z4_terms=" + std::to_string(nterms) + (plan.dpass[i] ? " stream" : "");
+        dsep += " z4_terms=" + std::to_string(nterms) + (plan.dpass[i] ? " stream" : "") +
+                (plan.hpass[i] ? " pipelined" : "");
         dsep += " phase_ops=[";
         for (int ph = 0; ph < A.nph; ++ph)
             dsep += std::to_string(A.ph[ph].op_end - A.ph[ph].op_begin) + (A.ph[ph].permuted ? "p" : "") +

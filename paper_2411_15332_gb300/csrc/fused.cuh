@@ -18,8 +18,10 @@ struct FusedPlan {
     std::vector<V> tabs;                  // diagonal tables to upload (PassArgs::tab)
     std::vector<unsigned char> dpass;     // 1: single-phase table pass for the streaming kernel
     std::vector<DPassArgs> dargs;         // its arguments (state / table pointers set at launch)
+    std::vector<unsigned char> hpass;     // 1: Hadamard / sign-term pass for the pipelined kernel
     bool resident = false;                // complex128 state kept as int64 fixed point (ENG_Q)
     int qguard = 0;                       // ENG_Q: headroom bits above the state norm
+    bool dither = false;                  // ENG_Q: a mixing gate follows the monomial body (dithered rounding)
 };
 
 // fp_only: every pass in the float engine (coefficients as plain values).

@@ -987,6 +987,330 @@ __global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
     }
 }
 
+// --------------------------------------------------- Hadamard passes --
+// Passes of butterflies and exact sign terms only (the Hadamard layers of
+// Sec. III-C's RH path), int64 engines, one state.  Persistent: two CTAs
+// per SM walk the tiles blockIdx.x, blockIdx.x + gridDim.x, ...; each
+// reads its tiles through one shared-memory buffer, and as soon as the last
+// phase of a tile has read the buffer the next tile's asynchronous copy
+// (cp.async) starts into it, overlapping that phase's arithmetic and
+// stores (the other CTA covers the rest).  Per-phase slot bases and
+// offsets are computed once per CTA; the tile base advances by a masked
+// add of the deposited grid stride ((tb | ~M) + dG) & M over the non-tile
+// mask M.  Every pass reads through the load staging map (the planner
+// stages the loads of these passes).
+constexpr int HP_CTAS_PER_SM = 2;
+constexpr int HP_MAXPH = 8;
+constexpr int HP_THREADS = 256;    // 2^(K - FR) for K = 12 tiles (fewer for smaller K)
+struct HPassArgs {
+    unsigned long long ntmask;     // non-tile global bits (below n)
+    unsigned long long dstride;    // gridDim.x deposited into the non-tile bits
+    unsigned ntiles;
+    unsigned salt;                 // ENG_Q: per-pass seed of the rounding dither
+    int dither;                    // ENG_Q: 1 = dithered rounding, 0 = to nearest (ties up)
+    unsigned long long gm[HP_MAXPH][FR];   // per phase: global bit of each register bit
+};
+
+// Dithered rounding (ENG_Q in this kernel).  After a Hadamard layer the
+// amplitudes of a state are often equal in magnitude; rounded the same way
+// they carry equal errors, which the next Hadamard layer adds up coherently
+// (2^(n/2) of them into one amplitude).  Each rounding of this kernel
+// therefore adds a pseudo-random increment u in [0, 2^k) before a k-bit
+// right shift: floor((v + u) / 2^k) is unbiased, and the errors of equal
+// amplitudes become uncorrelated.  u comes from a nonlinear hash (the
+// 32-bit finaliser of MurmurHash3) of the amplitude's global index, the
+// pass and the rounding site, so results do not depend on the launch shape
+// (a hash linear over GF(2) would correlate with the Walsh functions the
+// next layer projects on).  Circuits without a mixing gate after their
+// monomial body need no dither (nothing later concentrates the errors):
+// there d = 0x80008000 makes u = 2^(k-1), rounding to nearest.
+__device__ __forceinline__ uint32_t hp_hash(uint64_t g, uint32_t salt) {
+    uint32_t h = (uint32_t)g ^ ((uint32_t)(g >> 32) * 0x9E3779B9u) ^ salt;
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return h;
+}
+// 16 random bits d scaled to [0, 2^k), 1 <= k <= 63
+__device__ __forceinline__ long long hp_dk(uint32_t d16, int k) {
+    return (long long)(((unsigned long long)d16 << 48) >> (64 - k));
+}
+// x * c / 2^61 (Q61 constant c = ch * 2^31 + cl) with the final 30-bit
+// rounding dithered
+__device__ __forceinline__ long long hp_qmul_real(long long x, int ch, int cl, uint32_t d16) {
+    int h, l;
+    qsplit(x, h, l);
+    const long long m1 = (long long)h * ch;
+    const long long m2 = (long long)h * cl + (long long)l * ch + qlow(l, cl);
+    return 2 * m1 + ((m2 + ((long long)d16 << 14)) >> 30);
+}
+// d2fix with the rounding of dropped bits dithered
+__device__ __forceinline__ long long hp_d2fix(double v, int S, uint32_t d16) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)((b >> 52) & 0x7FF);
+    if (e == 0) return 0;
+    const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = S + e - 1075;
+    unsigned long long a;
+    if (sh >= 0) a = m << sh;
+    else if (sh > -64) a = (m + (unsigned long long)hp_dk(d16, -sh)) >> (-sh);
+    else a = 0;
+    return (b >> 63) ? -(long long)a : (long long)a;
+}
+
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(__cvta_generic_to_global(gsrc))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// (hi:lo) >> k for 0 <= k < 32 (arithmetic): two funnel shifts
+__device__ __forceinline__ long long shr_lt32(long long v, int k) {
+    const unsigned lo = (unsigned)v, hi = (unsigned)(v >> 32);
+    const unsigned nlo = __funnelshift_r(lo, hi, k);
+    const int nhi = (int)hi >> k;
+    return (long long)(((unsigned long long)(unsigned)nhi << 32) | nlo);
+}
+// 16 dither bits d scaled to [0, 2^k), 1 <= k < 32
+__device__ __forceinline__ long long dk_lt32(unsigned d16, int k) {
+    return (long long)(k <= 16 ? (d16 >> (16 - k)) : (d16 << (k - 16)));
+}
+// Dither of register slot j from the thread's hash t (a bijective multiply
+// of t ^ j's constant): re and im take two 16-bit fields.  Without dither
+// both are 0x8000 (round to nearest, ties up).
+__device__ __forceinline__ void hp_dj(uint32_t t, int j, bool dither, unsigned& re, unsigned& im) {
+    if (!dither) {
+        re = im = 0x8000u;
+        return;
+    }
+    const uint32_t d = (t ^ (0x9E3779B9u * (uint32_t)(j + 1))) * 0x2C1B3C6Du;
+    re = d >> 16;
+    im = (d >> 4) & 0xFFFFu;
+}
+
+template <int ENG, int QIN>
+__global__ void __launch_bounds__(HP_THREADS, HP_CTAS_PER_SM)
+    k_hpass(const __grid_constant__ PassArgs<double2> a, const __grid_constant__ HPassArgs h) {
+    static_assert(ENG == ENG_I64 || ENG == ENG_Q, "int64 engines only");
+    using V = I2;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ int s_emax[HP_THREADS / 32];
+    __shared__ unsigned long long s_gloc[HP_MAXPH][HP_THREADS];
+    __shared__ short s_sb[HP_MAXPH][HP_THREADS], s_ob[HP_MAXPH][HP_THREADS];
+    const int K = a.K;
+    const uint32_t T = 1u << (K - FR);
+    const uint32_t tid = threadIdx.x;
+    double2* const psi = a.psi;
+    double2* const pso = a.psi_out ? a.psi_out : a.psi;   // tiles are disjoint: out of place is free
+    int Sq = 0;
+    if constexpr (ENG == ENG_Q) Sq = *a.qS - a.qgi;
+    // per phase and thread (tile-independent): global offset of register
+    // slot 0, and the entry / exit slot bases in shared memory
+    for (int p = 0; p < a.nph; ++p) {
+        s_gloc[p][tid] = spread_bits(insert_reg_zeros(tid, a.ph[p].rb), a.tpos, K);
+        const int sb = xbase(a.ph[p].in, tid);
+        s_sb[p][tid] = (short)sb;
+        s_ob[p][tid] = (short)(a.ph[p].permuted ? (xbase(a.ph[p].out.s, tid) ^ (int)a.ph[p].out.off0) : sb);
+    }
+    // staged copy: element tid + i*T of the tile, its top FR local bits from i
+    const uint64_t gt = spread_bits(tid, a.tpos, K - FR);
+    uint64_t gtop[FR];
+    int lst[FR];
+#pragma unroll
+    for (int r = 0; r < FR; ++r) {
+        gtop[r] = 1ull << a.tpos[K - FR + r];
+        lst[r] = a.ld.rc[r];
+    }
+    const int ls0 = xbase(a.ld, tid);
+    const unsigned G = gridDim.x;
+    auto madd = [&](uint64_t tb) { return ((tb | ~h.ntmask) + h.dstride) & h.ntmask; };
+    double2* const sms = reinterpret_cast<double2*>(smraw);
+    V* const sm = reinterpret_cast<V*>(smraw);
+    auto prefetch = [&](uint64_t t, uint64_t tb) {
+        if (t < h.ntiles) {
+            const uint64_t g0 = tb | gt;
+#pragma unroll
+            for (int i = 0; i < FRA; ++i) cp_async16(sms + (ls0 ^ dep4x(i, lst)), psi + (g0 | dep4(i, gtop)));
+        }
+        cp_async_commit();
+    };
+    uint64_t tb = insert_zeros(blockIdx.x, a.tpos, K);   // base of the tile being worked on
+    __syncthreads();
+    prefetch(blockIdx.x, tb);
+    const bool dither = ENG == ENG_Q && h.dither;
+    for (uint64_t tile = blockIdx.x; tile < h.ntiles; tile += G) {
+        cp_async_wait<0>();
+        __syncthreads();   // this tile is in the buffer
+        const uint64_t tbn = madd(tb);
+        V x[FRA];
+        int S = Sq;
+        for (int p = 0; p < a.nph; ++p) {
+            const TilePhase& ph = a.ph[p];
+            const uint64_t gb = tb | s_gloc[p][tid];
+            uint64_t gm[FR];
+            int sr[FR];
+#pragma unroll
+            for (int r = 0; r < FR; ++r) {
+                gm[r] = h.gm[p][r];
+                sr[r] = ph.in.rc[r];
+            }
+            const int sb = s_sb[p][tid];
+            if (p == 0) {
+#pragma unroll
+                for (int j = 0; j < FRA; ++j) x[j] = raw_load<double2, V>(sms[sb ^ dep4x(j, sr)]);
+                if constexpr (ENG == ENG_Q && QIN == 1) {
+                    const uint32_t t = dither ? hp_hash(gb, h.salt) : 0u;
+#pragma unroll
+                    for (int j = 0; j < FRA; ++j) {
+                        unsigned dr, di;
+                        hp_dj(t, j, dither, dr, di);
+                        x[j].x = hp_d2fix(__longlong_as_double(x[j].x), S, dr);
+                        x[j].y = hp_d2fix(__longlong_as_double(x[j].y), S, di);
+                    }
+                }
+                if constexpr (ENG == ENG_I64) {
+                    int e = 0;
+#pragma unroll
+                    for (int j = 0; j < FRA; ++j)
+                        e = max(e, max((int)((x[j].x >> 52) & 0x7FF), (int)((x[j].y >> 52) & 0x7FF)));
+                    const unsigned amask = T >= 32 ? 0xffffffffu : ((1u << T) - 1u);
+                    e = (int)__reduce_max_sync(amask, (unsigned)e);
+                    if ((tid & 31) == 0) s_emax[tid >> 5] = e;
+                    __syncthreads();
+                    int emax = 0;
+                    for (int w = 0; w < (int)((T + 31) >> 5); ++w) emax = max(emax, s_emax[w]);
+                    S = emax == 0 ? 0 : 62 - a.guard - (emax - 1022);
+#pragma unroll
+                    for (int j = 0; j < FRA; ++j) {
+                        x[j].x = d2fix(__longlong_as_double(x[j].x), S);
+                        x[j].y = d2fix(__longlong_as_double(x[j].y), S);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < FRA; ++j) x[j] = sm[sb ^ dep4x(j, sr)];
+            }
+            if (p == a.nph - 1 && !a.store_smem) {
+                // the buffer is read: the next tile streams in under this phase
+                __syncthreads();
+                prefetch(tile + G, tbn);
+            }
+            for (int o = ph.op_begin; o < ph.op_end; ++o) {
+                const TileOp& op = a.ops[o];
+                if (op.type == TOP_H) {
+                    switch (op.a) {
+                    case 0: op_h<V, 0>(x); break;
+                    case 1: op_h<V, 1>(x); break;
+                    case 2: op_h<V, 2>(x); break;
+                    default: op_h<V, 3>(x); break;
+                    }
+                } else {
+                    op_z4<V>(x, op, a.z4, gb, gm);
+                }
+            }
+            int orr[FR];
+#pragma unroll
+            for (int r = 0; r < FR; ++r) orr[r] = ph.permuted ? ph.out.s.rc[r] : sr[r];
+            if (ph.permuted) __syncthreads();
+            const int ob = s_ob[p][tid];
+            if (p != a.nph - 1) {
+                if constexpr (ENG == ENG_Q) {
+                    if (ph.qsh > 0) {
+                        const int k = ph.qsh;
+                        const uint32_t t = dither ? hp_hash(gb, h.salt ^ (0x51ED27u * (uint32_t)(p + 1))) : 0u;
+#pragma unroll
+                        for (int j = 0; j < FRA; ++j) {
+                            unsigned dr, di;
+                            hp_dj(t, j, dither, dr, di);
+                            x[j].x = shr_lt32(x[j].x + dk_lt32(dr, k), k);
+                            x[j].y = shr_lt32(x[j].y + dk_lt32(di, k), k);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < FRA; ++j) sm[ob ^ dep4x(j, orr)] = x[j];
+                __syncthreads();
+                continue;
+            }
+            double2* out = reinterpret_cast<double2*>(x);
+            if constexpr (ENG == ENG_Q) {
+                // the pass's 2^(-qend/2) and the change to the next pass's
+                // format: one dithered (or nearest) shift, times 1/sqrt(2)
+                // for odd qend; then doubles unless the state stays fixed point
+                const int k = (a.qend >> 1) + (a.q_out ? a.qgo - a.qgi : 0);
+                const bool odd = a.qend & 1;
+                const int r2h = 759250124, r2l = 2134625280;   // round(2^61 / sqrt(2)) = r2h * 2^31 + r2l
+                const uint32_t t = dither ? hp_hash(gb, h.salt) : 0u;
+#pragma unroll
+                for (int j = 0; j < FRA; ++j) {
+                    long long vx = x[j].x, vy = x[j].y;
+                    unsigned dr, di;
+                    hp_dj(t, j, dither, dr, di);
+                    if (odd) {
+                        vx = hp_qmul_real(vx, r2h, r2l, dr);
+                        vy = hp_qmul_real(vy, r2h, r2l, di);
+                        hp_dj(t ^ 0x5BD1E995u, j, dither, dr, di);
+                    }
+                    if (k > 0) {
+                        vx = shr_lt32(vx + dk_lt32(dr, k), k);
+                        vy = shr_lt32(vy + dk_lt32(di, k), k);
+                    } else if (k < 0) {
+                        vx = (long long)((unsigned long long)vx << (-k));
+                        vy = (long long)((unsigned long long)vy << (-k));
+                    }
+                    if (a.q_out) {
+                        x[j].x = vx;
+                        x[j].y = vy;
+                    } else {
+                        x[j].x = __double_as_longlong(fix2d(vx, S));
+                        x[j].y = __double_as_longlong(fix2d(vy, S));
+                    }
+                }
+            } else {
+                const int So = S + (a.nh >> 1);
+                const bool odd = a.nh & 1;
+                const long long r2 = 3260954456333195553ll;   // round(2^62 / sqrt(2))
+#pragma unroll
+                for (int j = 0; j < FRA; ++j) {
+                    long long vx = x[j].x, vy = x[j].y;
+                    if (odd) {
+                        vx = __mul64hi(vx, r2) << 2;
+                        vy = __mul64hi(vy, r2) << 2;
+                    }
+                    x[j].x = __double_as_longlong(fix2d(vx, So));
+                    x[j].y = __double_as_longlong(fix2d(vy, So));
+                }
+            }
+            if (!a.store_smem) {
+#pragma unroll
+                for (int j = 0; j < FRA; ++j) __stcs(pso + (gb | dep4(j, gm)), out[j]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < FRA; ++j) sms[ob ^ dep4x(j, orr)] = out[j];
+                __syncthreads();
+                int st[FR];
+#pragma unroll
+                for (int r = 0; r < FR; ++r) st[r] = a.st.rc[r];
+                const int s0 = xbase(a.st, tid);
+                const uint64_t g0 = tb | gt;
+#pragma unroll
+                for (int i = 0; i < FRA; ++i) __stcs(pso + (g0 | dep4(i, gtop)), sms[s0 ^ dep4x(i, st)]);
+                __syncthreads();
+                prefetch(tile + G, tbn);
+            }
+        }
+        tb = tbn;
+    }
+    cp_async_wait<0>();
+}
+
 // ------------------------------------------------ single-phase tables --
 // A resident-engine pass whose only work is one phase of diagonal tables and
 // sign terms (its permutations ride on the gathered loads and scattered

@@ -14,4 +14,9 @@ const void* tile_fn_i64(int feat, int qin) {
     }
 }
 
+const void* tile_fn_hpass(int eng, int qin) {
+    if (eng == ENG_Q) return qin ? (const void*)k_hpass<ENG_Q, 1> : (const void*)k_hpass<ENG_Q, 0>;
+    return (const void*)k_hpass<ENG_I64, 0>;
+}
+
 }  // namespace mera

@@ -35,7 +35,7 @@ def parse(summary):
 
 def test_layered_n30_plan(core):
     head, passes = parse(core.plan_summary(30, inputs.layered_circuit(30, 20, seed=2)))
-    assert head["resident"] == 1 and head["passes"] == 60
+    assert head["resident"] == 1 and head["passes"] == 60 and head["dither"] == 0
     assert all(p["eng"] == "q" for p in passes)
     # the CNOT ladders ride on the exchanges: no register permutation op
     assert all(p["mono"] == "0" for p in passes)
@@ -78,11 +78,31 @@ def test_complex64_plans_use_the_float_engine(core):
     assert all(p["eng"] == "fp" for p in passes)
 
 
-def test_mixing_gates_after_the_body_keep_doubles(core):
-    """Grover: Hadamard layers after phase flips -- a global fixed-point
-    scale would let later butterflies concentrate rounding errors, so the
-    passes keep double storage (per-tile int64 for the butterflies)."""
+def test_mixing_gates_after_the_body_need_the_dithered_kernel(core):
+    """Grover: Hadamard layers after phase flips.  With one global scale,
+    equal amplitudes carry equal rounding errors that a later Hadamard layer
+    would add up coherently; the state stays fixed point only because every
+    tile pass runs the Hadamard-pass kernel, whose rounding is dithered."""
     ops, _ = inputs.grover_circuit(24, 4, seed=3)
-    head, passes = parse(core.plan_summary(24, ops))
+    summary = core.plan_summary(24, ops)
+    head, passes = parse(summary)
+    assert head["resident"] == 1 and head["dither"] == 1
+    assert all(p["eng"] == "q" for p in passes)
+    lines = summary.splitlines()[1:]
+    assert all("pipelined" in l for l in lines)
+    assert all(p["load_smem"] == "1" for p in passes)
+
+
+def test_mixing_gates_after_the_body_without_the_kernel_keep_doubles(core):
+    """A table pass (RZ on every qubit) between Hadamard layers does not run
+    the Hadamard-pass kernel, so that circuit keeps double storage (per-tile
+    int64 for the butterflies)."""
+    n = 20
+    rng = np.random.default_rng(5)
+    ops = inputs.hadamard_all(n)
+    ops += [op("Z", (q,)) for q in range(0, n, 3)]
+    ops += [op("RZ", (q,), (), (float(t),)) for q, t in enumerate(rng.uniform(0, 6.28, n))]
+    ops += inputs.hadamard_all(n)
+    head, passes = parse(core.plan_summary(n, ops))
     assert head["resident"] == 0
-    assert all(p["eng"] in ("i64", "fp") for p in passes)
+    assert all(p["eng"] in ("i64", "fp") for p in passes if not p.get("single"))
