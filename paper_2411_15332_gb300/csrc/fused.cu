@@ -1452,19 +1452,18 @@ static void dpass_args(const PassArgs<V>& A, int n, DPassArgs& d) {
     d.shift = A.q_out ? A.qgo - A.qgi : 0;
 }
 
-// A complex128 int64-engine pass of butterflies and sign terms only, without
-// gathered loads or scattered stores: the pipelined Hadamard-pass kernel.
+// A complex128 int64-engine pass of butterflies and sign terms only (a
+// closing permutation run may ride on its stores; none on its loads): the
+// Hadamard-pass kernel.
 template <typename V>
 static bool hpass_ok(const PassArgs<V>& A, int eng, int K) {
     if (sizeof(V) != 16 || (eng != ENG_I64 && eng != ENG_Q)) return false;
-    if (A.gather || A.scatter || A.nph > HP_MAXPH || (1 << (K - FR)) > HP_THREADS) return false;
-    for (int p = 0; p < A.nph; ++p)
-        if (A.ph[p].out.noff != 0) return false;   // no tile-dependent exit offsets
+    if (A.gather || A.nph > HP_MAXPH || (1 << (K - FR)) > HP_THREADS) return false;
     if (((size_t)1 << K) * sizeof(V) > 64 * 1024) return false;
     for (int p = 0; p < A.nph; ++p)
         for (int o = A.ph[p].op_begin; o < A.ph[p].op_end; ++o) {
             const TileOp& op = A.ops[o];
-            if (!(op.type == TOP_H || (op.type == TOP_Z4 && op.c == 0))) return false;
+            if (!(op.type == TOP_H || (op.type == TOP_Z4 && (op.c == 0 || (op.c == 2 && A.scatter))))) return false;
         }
     return true;
 }
@@ -1965,7 +1964,7 @@ static int describe_fused(int n, int dtype, const std::vector<PrepOp>& ops, std:
         for (int o = 0; o < nop; ++o)
             if (A.ops[o].type == TOP_Z4) nterms += A.ops[o].aux2;
         dsep += " z4_terms=" + std::to_string(nterms) + (plan.dpass[i] ? " stream" : "") +
-                (plan.hpass[i] ? " pipelined" : "");
+                (plan.hpass[i] ? " pipelined" : "") + (A.gather ? " gather" : "") + (A.scatter ? " scatter" : "");
         dsep += " phase_ops=[";
         for (int ph = 0; ph < A.nph; ++ph)
             dsep += std::to_string(A.ph[ph].op_end - A.ph[ph].op_begin) + (A.ph[ph].permuted ? "p" : "") +

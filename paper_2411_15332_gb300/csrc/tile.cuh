@@ -1129,6 +1129,20 @@ __global__ void __launch_bounds__(HP_THREADS, HP_CTAS_PER_SM)
         lst[r] = a.ld.rc[r];
     }
     const int ls0 = xbase(a.ld, tid);
+    // scattered store (a closing permutation run): the thread's part of
+    // the map; the tile's part is added per tile
+    uint64_t gsc = 0;
+    if constexpr (ENG == ENG_Q) {
+        gsc = a.gout.c;
+#pragma unroll
+        for (int t = 0; t < 12; ++t) gsc ^= (0ull - (uint64_t)((tid >> t) & 1u)) & a.gout.tc[t];
+    }
+    auto scatter_base = [&](uint64_t tb) {
+        uint64_t v = tb ^ gsc;
+        for (int i = 0; i < a.gout.nq; ++i)
+            if ((tb >> a.gout.q[i]) & 1ull) v ^= a.gout.w[i];
+        return v;
+    };
     const unsigned G = gridDim.x;
     auto madd = [&](uint64_t tb) { return ((tb | ~h.ntmask) + h.dstride) & h.ntmask; };
     double2* const sms = reinterpret_cast<double2*>(smraw);
@@ -1211,6 +1225,20 @@ __global__ void __launch_bounds__(HP_THREADS, HP_CTAS_PER_SM)
                     case 2: op_h<V, 2>(x); break;
                     default: op_h<V, 3>(x); break;
                     }
+                } else if (ENG == ENG_Q && op.c == 2) {
+                    // sign terms after the closing permutation: on the store index
+                    const uint64_t g0 = scatter_base(tb);
+                    int e[FRA];
+#pragma unroll
+                    for (int j = 0; j < FRA; ++j) e[j] = 0;
+                    for (int t = 0; t < op.aux2; ++t) {
+                        const Z4Term z = a.z4[op.aux + t];
+#pragma unroll
+                        for (int j = 0; j < FRA; ++j)
+                            if (((g0 ^ dep4xl(j, a.gout.rc)) & z.mask) == z.vals) e[j] += z.e;
+                    }
+#pragma unroll
+                    for (int j = 0; j < FRA; ++j) x[j] = mul_ik(x[j], e[j] & 3);
                 } else {
                     op_z4<V>(x, op, a.z4, gb, gm);
                 }
@@ -1219,7 +1247,9 @@ __global__ void __launch_bounds__(HP_THREADS, HP_CTAS_PER_SM)
 #pragma unroll
             for (int r = 0; r < FR; ++r) orr[r] = ph.permuted ? ph.out.s.rc[r] : sr[r];
             if (ph.permuted) __syncthreads();
-            const int ob = s_ob[p][tid];
+            int ob = s_ob[p][tid];
+            for (int i = 0; i < ph.out.noff; ++i)
+                if ((gb >> ph.out.offq[i]) & 1ull) ob ^= (int)ph.out.offv[i];
             if (p != a.nph - 1) {
                 if constexpr (ENG == ENG_Q) {
                     if (ph.qsh > 0) {
@@ -1288,7 +1318,14 @@ __global__ void __launch_bounds__(HP_THREADS, HP_CTAS_PER_SM)
                     x[j].y = __double_as_longlong(fix2d(vy, So));
                 }
             }
-            if (!a.store_smem) {
+            if (ENG == ENG_Q && a.scatter) {
+                const uint64_t g0 = scatter_base(tb);
+                uint64_t rc[FR];
+#pragma unroll
+                for (int r = 0; r < FR; ++r) rc[r] = a.gout.rc[r];
+#pragma unroll
+                for (int j = 0; j < FRA; ++j) __stcs(pso + (g0 ^ dep4xl(j, rc)), out[j]);
+            } else if (!a.store_smem) {
 #pragma unroll
                 for (int j = 0; j < FRA; ++j) __stcs(pso + (gb | dep4(j, gm)), out[j]);
             } else {
