@@ -1749,6 +1749,22 @@ int fused_launch(const FusedPlan<V>& plan, size_t i, PassArgs<V>& A, unsigned ny
         h.dither = plan.dither ? 1 : 0;
         for (int ph = 0; ph < A.nph; ++ph)
             for (int r = 0; r < FR; ++r) h.gm[ph][r] = 1ull << A.tpos[A.ph[ph].rb[r]];
+        // runs of butterflies on distinct register bits (they commute: one block)
+        memset(h.hrun, 0, sizeof(h.hrun));
+        for (int ph = 0; ph < A.nph; ++ph)
+            for (int o = A.ph[ph].op_begin; o < A.ph[ph].op_end;) {
+                if (A.ops[o].type != TOP_H) {
+                    ++o;
+                    continue;
+                }
+                int m = 0, len = 0;
+                while (o + len < A.ph[ph].op_end && A.ops[o + len].type == TOP_H && !((m >> A.ops[o + len].a) & 1)) {
+                    m |= 1 << A.ops[o + len].a;
+                    ++len;
+                }
+                h.hrun[o] = (unsigned char)(m | (len << 4));
+                o += len;
+            }
         const void* fn = tile_fn_hpass(plan.eng[i], plan.eng[i] == ENG_Q && !A.q_in ? 1 : 0);
         const size_t hsm = ((size_t)1 << K) * sizeof(V);
         static std::vector<std::pair<const void*, size_t>> opted;

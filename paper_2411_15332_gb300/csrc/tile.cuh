@@ -505,9 +505,18 @@ __device__ __forceinline__ void op_h(V (&x)[FRA]) {
     for (int j = 0; j < FRA; ++j) {
         if (j & (1 << B)) continue;
         const int j1 = j | (1 << B);
-        const V a0 = x[j], a1 = x[j1];
-        x[j] = vadd(a0, a1);
-        x[j1] = vsub(a0, a1);
+        if constexpr (IsFP<V>::value) {
+            const V a0 = x[j], a1 = x[j1];
+            x[j] = vadd(a0, a1);
+            x[j1] = vsub(a0, a1);
+        } else {
+            // integers: a - b = (a + b) - b - b exactly, so both results
+            // overwrite their operands without a temporary
+            x[j].x += x[j1].x;
+            x[j].y += x[j1].y;
+            x[j1].x = x[j].x - x[j1].x - x[j1].x;
+            x[j1].y = x[j].y - x[j1].y - x[j1].y;
+        }
     }
 }
 
@@ -1009,6 +1018,9 @@ struct HPassArgs {
     unsigned salt;                 // ENG_Q: per-pass seed of the rounding dither
     int dither;                    // ENG_Q: 1 = dithered rounding, 0 = to nearest (ties up)
     unsigned long long gm[HP_MAXPH][FR];   // per phase: global bit of each register bit
+    // per op: a run of butterflies on distinct register bits starting here
+    // (bits 0..3: the bits, bits 4..7: the run's length in ops), else 0
+    unsigned char hrun[TILE_MAX_OPS];
 };
 
 // Dithered rounding (ENG_Q in this kernel).  After a Hadamard layer the
@@ -1093,6 +1105,23 @@ __device__ __forceinline__ void hp_dj(uint32_t t, int j, bool dither, unsigned& 
     const uint32_t d = (t ^ (0x9E3779B9u * (uint32_t)(j + 1))) * 0x2C1B3C6Du;
     re = d >> 16;
     im = (d >> 4) & 0xFFFFu;
+}
+
+// Butterflies on the register bits set in m: a full phase (all four bits)
+// as one straight block, otherwise bit by bit.
+template <typename V>
+__device__ __forceinline__ void op_hmask(V (&x)[FRA], int m) {
+    if (m == 15) {
+        op_h<V, 0>(x);
+        op_h<V, 1>(x);
+        op_h<V, 2>(x);
+        op_h<V, 3>(x);
+        return;
+    }
+    if (m & 1) op_h<V, 0>(x);
+    if (m & 2) op_h<V, 1>(x);
+    if (m & 4) op_h<V, 2>(x);
+    if (m & 8) op_h<V, 3>(x);
 }
 
 template <int ENG, int QIN>
@@ -1216,16 +1245,16 @@ __global__ void __launch_bounds__(HP_THREADS, HP_CTAS_PER_SM)
                 __syncthreads();
                 prefetch(tile + G, tbn);
             }
-            for (int o = ph.op_begin; o < ph.op_end; ++o) {
+            for (int o = ph.op_begin; o < ph.op_end;) {
                 const TileOp& op = a.ops[o];
                 if (op.type == TOP_H) {
-                    switch (op.a) {
-                    case 0: op_h<V, 0>(x); break;
-                    case 1: op_h<V, 1>(x); break;
-                    case 2: op_h<V, 2>(x); break;
-                    default: op_h<V, 3>(x); break;
-                    }
-                } else if (ENG == ENG_Q && op.c == 2) {
+                    const int r = h.hrun[o];
+                    op_hmask<V>(x, r & 15);
+                    o += max(r >> 4, 1);   // (a run covers at least this op)
+                    continue;
+                }
+                ++o;
+                if (ENG == ENG_Q && op.c == 2) {
                     // sign terms after the closing permutation: on the store index
                     const uint64_t g0 = scatter_base(tb);
                     int e[FRA];
