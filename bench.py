@@ -299,9 +299,14 @@ def _arith_note(args):
     if args.dtype == "c64":
         return "float32 state and arithmetic, float64 reductions"
     if args.mode == "fused":
-        return ("complex128 state held as int64 fixed point across the circuit's tile passes "
+        note = ("complex128 state held as int64 fixed point across the circuit's tile passes "
                 "(global scale from a norm bound; exact butterflies and moves; 31-bit-limb integer "
-                "products for phases, unbiased rounding); float64 at the circuit's ends and in reductions")
+                "products for phases, rounding to nearest); float64 at the circuit's ends and in reductions")
+        if args.workload == "grover":
+            note = note.replace("rounding to nearest", "roundings dithered by a hash of the amplitude index, "
+                                "since Hadamard layers follow the sign flips; an odd level's sqrt(2) carried "
+                                "to the next pass")
+        return note
     return "float64 per-gate kernels"
 
 
@@ -364,7 +369,7 @@ def run_mera(args, rank, world, local_rank):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None,
                 "traffic": tr["dram_bytes_per_launch"] if tr else None,
-                "kernel": "k_tile (fused tile passes)" if kcls == "tile" else "per-gate kernels",
+                "kernel": "k_hpass / k_dpass / k_tile (fused tile passes)" if kcls == "tile" else "per-gate kernels",
                 "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                 "kernel_launches": nl, "kernel_ms": kms,
                 "kernel_share": kms / total_ms if total_ms else None,
