@@ -1749,6 +1749,25 @@ int fused_launch(const FusedPlan<V>& plan, size_t i, PassArgs<V>& A, unsigned ny
         h.dither = plan.dither ? 1 : 0;
         for (int ph = 0; ph < A.nph; ++ph)
             for (int r = 0; r < FR; ++r) h.gm[ph][r] = 1ull << A.tpos[A.ph[ph].rb[r]];
+        // parity masks of the sign terms on the scattered store index
+        memset(h.pz, 0, sizeof(h.pz));
+        for (int ph = 0; ph < A.nph; ++ph)
+            for (int o = A.ph[ph].op_begin; o < A.ph[ph].op_end; ++o) {
+                const TileOp& op = A.ops[o];
+                if (op.type != TOP_Z4 || op.c != 2) continue;
+                for (int t = 0; t < op.aux2; ++t) {
+                    uint64_t m = A.z4[op.aux + t].mask;
+                    for (int k = 0; k < 2 && m; ++k) {
+                        const int q = __builtin_ctzll(m);
+                        m &= m - 1;
+                        static const unsigned b1[4] = {0xAAAAu, 0xCCCCu, 0xF0F0u, 0xFF00u};
+                        unsigned pq = 0;
+                        for (int r = 0; r < FR; ++r)
+                            if ((A.gout.rc[r] >> q) & 1ull) pq ^= b1[r];
+                        h.pz[op.aux + t] |= pq << (16 * k);
+                    }
+                }
+            }
         // runs of butterflies on distinct register bits (they commute: one block)
         memset(h.hrun, 0, sizeof(h.hrun));
         for (int ph = 0; ph < A.nph; ++ph)

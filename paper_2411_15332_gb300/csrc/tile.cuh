@@ -1021,6 +1021,10 @@ struct HPassArgs {
     // per op: a run of butterflies on distinct register bits starting here
     // (bits 0..3: the bits, bits 4..7: the run's length in ops), else 0
     unsigned char hrun[TILE_MAX_OPS];
+    // sign terms on the scattered store index: bit j of P(q) is the parity
+    // of the register bits of slot j that reach index bit q through the
+    // scatter map; the first two pattern bits' P in the low / high halves
+    unsigned pz[TILE_MAX_Z4];
 };
 
 // Dithered rounding (ENG_Q in this kernel).  After a Hadamard layer the
@@ -1255,19 +1259,44 @@ __global__ void __launch_bounds__(HP_THREADS, HP_CTAS_PER_SM)
                 }
                 ++o;
                 if (ENG == ENG_Q && op.c == 2) {
-                    // sign terms after the closing permutation: on the store index
+                    // sign terms after the closing permutation, on the store
+                    // index: bit q of slot j's index is bit q of the thread's
+                    // base XOR the parity P(q) of j, so the slots a term
+                    // selects form one 16-bit mask per thread
                     const uint64_t g0 = scatter_base(tb);
-                    int e[FRA];
-#pragma unroll
-                    for (int j = 0; j < FRA; ++j) e[j] = 0;
+                    uint32_t p0 = 0, p1 = 0;
                     for (int t = 0; t < op.aux2; ++t) {
                         const Z4Term z = a.z4[op.aux + t];
+                        const uint32_t pm = h.pz[op.aux + t];
+                        const uint64_t tv = z.vals ^ g0;
+                        uint64_t m = z.mask;
+                        uint32_t act = 0xFFFFu;
+                        for (int k = 0; m; ++k) {
+                            const int q = __ffsll((long long)m) - 1;
+                            m &= m - 1;
+                            uint32_t pq = 0;
+                            if (k < 2) {
+                                pq = (pm >> (16 * k)) & 0xFFFFu;
+                            } else {
+                                const uint32_t b1[4] = {0xAAAAu, 0xCCCCu, 0xF0F0u, 0xFF00u};
+#pragma unroll
+                                for (int r = 0; r < FR; ++r)
+                                    if ((a.gout.rc[r] >> q) & 1ull) pq ^= b1[r];
+                            }
+                            act &= ((tv >> q) & 1ull) ? pq : (~pq & 0xFFFFu);
+                        }
+                        if (z.e & 1) {
+                            const uint32_t c = p0 & act;
+                            p0 ^= act;
+                            p1 ^= c;
+                        }
+                        if (z.e & 2) p1 ^= act;
+                    }
+                    if ((p0 | p1) != 0) {
 #pragma unroll
                         for (int j = 0; j < FRA; ++j)
-                            if (((g0 ^ dep4xl(j, a.gout.rc)) & z.mask) == z.vals) e[j] += z.e;
+                            x[j] = mul_ik(x[j], (int)(((p0 >> j) & 1u) | (((p1 >> j) & 1u) << 1)));
                     }
-#pragma unroll
-                    for (int j = 0; j < FRA; ++j) x[j] = mul_ik(x[j], e[j] & 3);
                 } else {
                     op_z4<V>(x, op, a.z4, gb, gm);
                 }
