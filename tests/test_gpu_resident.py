@@ -124,3 +124,62 @@ def test_runs_split_by_per_gate_ops(layers):
     ref = sv.apply_matrix(ref, n, perm8, (9, 2, 13))
     ref = sv.simulate(n, second, psi0=ref)
     assert max_err(got, ref) <= 1e-13
+
+
+def _grover_split(n):
+    """Hadamard layers after sign flips, split into two runs by a
+    three-target gate; the partial layer on even qubits gives the first run
+    an odd level count somewhere."""
+    m = inputs.grover_marked(n, seed=7)
+    perm8 = np.roll(np.eye(8, dtype=np.complex128), 1, axis=0)
+    first = inputs.hadamard_all(n) + [inputs.flip_index(n, m)] + [op("H", (q,)) for q in range(0, n, 2)]
+    second = ([inputs.flip_index(n, 0)] + inputs.hadamard_all(n) + [inputs.flip_index(n, m)]
+              + inputs.hadamard_all(n))
+    return first, perm8, second
+
+
+@pytest.mark.parametrize("n", [14, 17])
+def test_dithered_runs_split_by_per_gate_ops(n):
+    """Resident with dithered rounding (mixing gates after sign flips): a
+    per-gate op ends the first run, whose last pass must take the sqrt(2) an
+    odd level count left pending before writing doubles; the second run
+    starts afresh."""
+    first, perm8, second = _grover_split(n)
+    s = new_state(n)
+    s.apply_circuit(first + [(perm8, (n - 1, 3, 6), (), (), 0)] + second, mode="fused")
+    got = s.to_numpy()
+    s.close()
+    ref = sv.simulate(n, first)
+    ref = sv.apply_matrix(ref, n, perm8, (n - 1, 3, 6))
+    ref = sv.simulate(n, second, psi0=ref)
+    assert max_err(got, ref) <= 1e-13
+
+
+def test_dithered_conversion_of_a_general_state():
+    """The first pass of a dithered run converts arbitrary doubles (not a
+    basis state) into the fixed-point format."""
+    n = 16
+    rng = np.random.default_rng(44)
+    psi = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+    psi /= np.linalg.norm(psi)
+    ops, _ = inputs.grover_circuit(n, 2, seed=3)
+    s = new_state(n, psi=psi)
+    s.apply_circuit(ops, mode="fused")
+    got = s.to_numpy()
+    s.close()
+    ref = sv.simulate(n, ops, psi0=psi)
+    assert max_err(got, ref) <= 1e-13
+
+
+def test_dithered_rounding_is_reproducible():
+    """The dither comes from a hash of the amplitude index, the pass and the
+    rounding site: the same circuit gives bitwise the same state."""
+    n = 20
+    ops, _ = inputs.grover_circuit(n, 3, seed=3)
+    outs = []
+    for _ in range(2):
+        s = new_state(n)
+        s.apply_circuit(ops, mode="fused")
+        outs.append(s.to_numpy())
+        s.close()
+    assert np.array_equal(outs[0].view(np.uint64), outs[1].view(np.uint64))

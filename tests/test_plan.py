@@ -106,3 +106,18 @@ def test_mixing_gates_after_the_body_without_the_kernel_keep_doubles(core):
     head, passes = parse(core.plan_summary(n, ops))
     assert head["resident"] == 0
     assert all(p["eng"] in ("i64", "fp") for p in passes if not p.get("single"))
+
+def test_dithered_plan_split_by_a_per_gate_op(core):
+    """A three-target gate between Hadamard layers and sign flips: two runs
+    of Hadamard-pass kernels, still resident with dithered rounding."""
+    n = 17
+    m = inputs.grover_marked(n, seed=7)
+    perm8 = np.roll(np.eye(8, dtype=np.complex128), 1, axis=0)
+    ops = (inputs.hadamard_all(n) + [inputs.flip_index(n, m)] + [op("H", (q,)) for q in range(0, n, 2)]
+           + [(perm8, (n - 1, 3, 6), (), (), 0)] + [inputs.flip_index(n, 0)] + inputs.hadamard_all(n))
+    summary = core.plan_summary(n, ops)
+    head, passes = parse(summary)
+    assert head["resident"] == 1 and head["dither"] == 1
+    assert sum(1 for p in passes if p.get("single")) == 1
+    tile = [l for l in summary.splitlines()[1:] if "per-gate" not in l]
+    assert tile and all("pipelined" in l for l in tile)
