@@ -1,0 +1,59 @@
+"""The Hadamard-pass kernel (butterflies and sign terms; persistent, the
+next tile copied asynchronously under the last phase) against the oracle:
+whole-state tiles of a few threads (n < 12), and the per-tile int64 engine
+it also runs for circuits that keep double storage."""
+import numpy as np
+import pytest
+
+from oracle import statevector as sv
+from paper_2411_15332_gb300 import inputs
+from paper_2411_15332_gb300.inputs import op
+from tests.gpu_helpers import lib_ready, max_err, new_state
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _ready():
+    lib_ready()
+
+
+def _pipelined(n, ops):
+    from paper_2411_15332_gb300 import core
+    lines = core.plan_summary(n, ops).splitlines()
+    return lines[0], [l for l in lines[1:] if "per-gate" not in l]
+
+
+@pytest.mark.parametrize("n", [5, 6, 8, 11])
+def test_small_states(n):
+    """n < 12: one tile of 2^(n-4) threads (fewer than a warp for n < 9)."""
+    ops, m = inputs.grover_circuit(n, 3, seed=3)
+    head, tile = _pipelined(n, ops)
+    assert "dither=1" in head and all("pipelined" in l for l in tile)
+    s = new_state(n)
+    s.apply_circuit(ops, mode="fused")
+    got = s.to_numpy()
+    s.close()
+    assert max_err(got, sv.simulate(n, ops)) <= 1e-13
+
+
+@pytest.mark.parametrize("n", [7, 20])
+def test_per_tile_engine(n):
+    """Hadamard layers around a table pass (RZ on every qubit) keep double
+    storage: the Hadamard passes run the kernel's per-tile int64 engine
+    (block exponent from a tile max, conversions in and out)."""
+    rng = np.random.default_rng(50 + n)
+    ops = inputs.hadamard_all(n)
+    ops += [op("Z", (q,)) for q in range(0, n, 3)]
+    ops += [op("RZ", (q,), (), (float(t),)) for q, t in enumerate(rng.uniform(0, 6.28, n))]
+    ops += inputs.hadamard_all(n)
+    ops += [inputs.flip_index(n, int(rng.integers(0, 1 << n)))]
+    ops += [op("H", (q,)) for q in range(1, n, 2)]
+    head, tile = _pipelined(n, ops)
+    assert "resident=0" in head
+    assert any("eng=i64" in l and "pipelined" in l for l in tile)
+    s = new_state(n)
+    s.apply_circuit(ops, mode="fused")
+    got = s.to_numpy()
+    s.close()
+    assert max_err(got, sv.simulate(n, ops)) <= 1e-13
