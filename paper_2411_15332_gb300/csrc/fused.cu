@@ -18,6 +18,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1332,6 +1333,22 @@ static int round_feat(int, int feat, bool c128) {
     return FEAT_ALL;
 }
 
+// Raise a kernel's dynamic shared-memory limit to at least `bytes` (above
+// the 48 KiB default).  The limit only ever grows: a smaller tile of the
+// same kernel must not lower it under a larger one launched earlier.
+static int opt_in_smem(const void* fn, size_t bytes) {
+    static std::mutex mu;
+    static std::vector<std::pair<const void*, size_t>> limit;
+    if (bytes <= 48 * 1024) return MERA_OK;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = std::find_if(limit.begin(), limit.end(), [&](const std::pair<const void*, size_t>& e) { return e.first == fn; });
+    if (it != limit.end() && it->second >= bytes) return MERA_OK;
+    MERA_CHECK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    if (it != limit.end()) it->second = bytes;
+    else limit.push_back(std::make_pair(fn, bytes));
+    return MERA_OK;
+}
+
 template <typename V>
 static int launch_tile(int eng, int feat, dim3 grid, unsigned block, size_t smem, cudaStream_t st,
                        const PassArgs<V>& A);
@@ -1340,11 +1357,7 @@ int launch_tile<double2>(int eng, int feat, dim3 grid, unsigned block, size_t sm
                          const PassArgs<double2>& A) {
     const void* fn = tile_fn_c128(eng, feat, eng == ENG_Q && !A.q_in ? 1 : 0);
     // opt in to the tile's dynamic shared memory (once per variant and size)
-    static std::vector<std::pair<const void*, size_t>> opted;
-    if (smem > 48 * 1024 && std::find(opted.begin(), opted.end(), std::make_pair(fn, smem)) == opted.end()) {
-        MERA_CHECK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        opted.push_back(std::make_pair(fn, smem));
-    }
+    MERA_TRY(opt_in_smem(fn, smem));
     void* args[] = {const_cast<PassArgs<double2>*>(&A)};
     MERA_CHECK_CUDA(cudaLaunchKernel(fn, grid, dim3(block), args, smem, st));
     return MERA_OK;
@@ -1786,11 +1799,7 @@ int fused_launch(const FusedPlan<V>& plan, size_t i, PassArgs<V>& A, unsigned ny
             }
         const void* fn = tile_fn_hpass(plan.eng[i], plan.eng[i] == ENG_Q && !A.q_in ? 1 : 0);
         const size_t hsm = ((size_t)1 << K) * sizeof(V);
-        static std::vector<std::pair<const void*, size_t>> opted;
-        if (std::find(opted.begin(), opted.end(), std::make_pair(fn, hsm)) == opted.end()) {
-            MERA_CHECK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm));
-            opted.push_back(std::make_pair(fn, hsm));
-        }
+        MERA_TRY(opt_in_smem(fn, hsm));
         void* args[] = {reinterpret_cast<void*>(&A), &h};
         MERA_CHECK_CUDA(cudaLaunchKernel(fn, dim3(ctas), dim3(1u << (K - FR)), args, hsm, st));
         return launch_end(st);

@@ -57,3 +57,16 @@ def test_per_tile_engine(n):
     got = s.to_numpy()
     s.close()
     assert max_err(got, sv.simulate(n, ops)) <= 1e-13
+
+
+def test_small_then_full_tiles():
+    """The same kernel variant with a whole-state tile of a few hundred
+    bytes, then a full 64 KiB tile, then small again: a kernel's dynamic
+    shared-memory limit may only grow between launches."""
+    for n in (6, 14, 7, 14):
+        ops, _ = inputs.grover_circuit(n, 1, seed=3)
+        s = new_state(n)
+        s.apply_circuit(ops, mode="fused")
+        got = s.to_numpy()
+        s.close()
+        assert max_err(got, sv.simulate(n, ops)) <= 1e-13
