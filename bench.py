@@ -365,10 +365,14 @@ def run_mera(args, rank, world, local_rank):
     kcls = "tile" if args.mode == "fused" else "gate"
     nl, kms, kbytes = prof[kcls]
     achieved = (kbytes / nl) / (kms / nl / 1e3) / 1e9 if nl else None
-    tr = _ncu_traffic()
+    # DRAM traffic per launch from the committed ncu capture: only for the
+    # kernels and workload it was taken on (the layered circuit's tile
+    # passes), scaled from n = 28 by the state size
+    tr = _ncu_traffic() if (kcls == "tile" and args.workload == "layered") else None
+    traffic = tr["dram_bytes_per_launch_n28"] * 2.0 ** (args.n - 28) if tr else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None,
-                "traffic": tr["dram_bytes_per_launch"] if tr else None,
+                "traffic": traffic,
                 "kernel": "k_hpass / k_dpass / k_tile (fused tile passes)" if kcls == "tile" else "per-gate kernels",
                 "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                 "kernel_launches": nl, "kernel_ms": kms,

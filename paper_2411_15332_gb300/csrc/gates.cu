@@ -316,6 +316,7 @@ static int launch_prepared(mera_state* s, const PrepOp& P) {
         // one target: a dense 2x2, or a swap with phases (X, Y, CNOT ...)
         const bool mono = P.kind == KIND_MONO;
         for (int j = 0; j < 4; ++j) a.m[j] = to_v<V>(P.m[j]);
+        a.hmode = !mono && P.m[0].imag() == 0.0 && P.m[1] == P.m[0] && P.m[2] == P.m[0] && P.m[3] == -P.m[0];
         for (int r = 0; r < 2; ++r) {
             a.v[r] = to_v<V>(P.v[r]);
             a.code[r] = phase_code(P.v[r]);

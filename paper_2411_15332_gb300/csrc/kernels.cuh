@@ -39,6 +39,24 @@ __device__ __forceinline__ V cdot2(V m0, V x0, V m1, V x1) {
     V acc = cmul(m0, x0);
     return cfma(m1, x1, acc);
 }
+template <typename V>
+__device__ __forceinline__ V vsum(V a, V b) {
+    a.x += b.x;
+    a.y += b.y;
+    return a;
+}
+template <typename V>
+__device__ __forceinline__ V vdiff(V a, V b) {
+    a.x -= b.x;
+    a.y -= b.y;
+    return a;
+}
+template <typename V, typename R>
+__device__ __forceinline__ V vscale(V a, R r) {
+    a.x *= r;
+    a.y *= r;
+    return a;
+}
 
 // int64 fixed-point complex (block floating point inside a fused tile).
 // Coefficients are Q62: value * 2^62 as int64 (|value| < 2).
@@ -142,6 +160,7 @@ struct GateArgs {
     int perm[8];                 // monomial: source sub-index of act[j]
     int flag[8];                 // diag: value != 1 for sub-index s
     int code[8];                 // phase code of v[] (see apply_phase)
+    int hmode;                   // one target: 1 = the real butterfly r [[1, 1], [1, -1]] (r = m[0].x)
     V v[8];                      // monomial / diag values
     V m[64];                     // dense matrix, row-major
 };
@@ -180,6 +199,13 @@ __device__ __forceinline__ void pair_update(const GateArgs<V>& a, V& x0, V& x1) 
         const V n1 = apply_phase(a.code[1], a.v[1], x0);
         x0 = n0;
         x1 = n1;
+    } else if (a.hmode) {
+        // Hadamard-type: two adds and two multiplies per component pair
+        // instead of a general complex 2x2 product
+        const auto r = a.m[0].x;
+        const V n0 = vsum(x0, x1), n1 = vdiff(x0, x1);
+        x0 = vscale(n0, r);
+        x1 = vscale(n1, r);
     } else {
         const V n0 = cdot2(a.m[0], x0, a.m[1], x1);
         const V n1 = cdot2(a.m[2], x0, a.m[3], x1);
@@ -240,6 +266,7 @@ __global__ void __launch_bounds__(256) k_dense1_shfl(const __grid_constant__ Gat
         const V y = shfl_xor_v(x, lm);
         const int hi = (int)((t >> a.qc) & 1ull);
         if (MONO) a.psi[i] = apply_phase(a.code[hi], a.v[hi], y);
+        else if (a.hmode) a.psi[i] = vscale(hi ? vdiff(y, x) : vsum(x, y), m0.x);
         else a.psi[i] = hi ? cdot2(m2, y, m3, x) : cdot2(m0, x, m1, y);
     }
 }

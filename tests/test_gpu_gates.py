@@ -175,3 +175,25 @@ def test_invalid_ops_leave_state_unchanged():
                 s.apply_circuit(ops, mode=mode)
             assert ei.value.code == L.MERA_EINVAL
     assert np.array_equal(s.to_numpy(), psi0)
+
+
+def test_diagonal_gates_on_both_product_paths():
+    """Per-gate complex128 diagonals: general unit phases take the FP64
+    multiply in 3 of 8 warps and the integer Q62 product in the others; a
+    diagonal with |Re| > 1 stays on the FP64 multiply everywhere."""
+    n = 16
+    rng = np.random.default_rng(12)
+    psi = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+    psi /= np.linalg.norm(psi)
+    mats = [(np.diag(np.exp(1j * rng.uniform(0, 6.28, 2))), (3,), (), 0),
+            (np.diag(np.exp(1j * rng.uniform(0, 6.28, 4))), (15, 0), (7,), 1),
+            (np.diag([2.0 + 0.0j, 0.5j]), (9,), (), 0),
+            (np.diag(np.exp(1j * rng.uniform(0, 6.28, 2))), (12,), (1, 4), 2)]
+    s = new_state(n, "c128", psi=psi)
+    s.apply_circuit([(G, t, c, (), cv) for G, t, c, cv in mats], mode="per_gate")
+    got = s.to_numpy()
+    s.close()
+    ref = psi.copy()
+    for G, t, c, cv in mats:
+        sv.apply_matrix(ref, n, G, t, c, cv)
+    assert max_err(got, ref) <= 1e-13
