@@ -1333,13 +1333,14 @@ static int round_feat(int, int feat, bool c128) {
     return FEAT_ALL;
 }
 
-// Raise a kernel's dynamic shared-memory limit to at least `bytes` (above
-// the 48 KiB default).  The limit only ever grows: a smaller tile of the
-// same kernel must not lower it under a larger one launched earlier.
+// Raise a kernel's dynamic shared-memory limit to at least `bytes` (the
+// 48 KiB default covers static plus dynamic shared memory, so a kernel with
+// static arrays needs the opt-in below 48 KiB of dynamic memory too).  The
+// limit only ever grows: a smaller tile of the same kernel must not lower
+// it under a larger one launched earlier.
 static int opt_in_smem(const void* fn, size_t bytes) {
     static std::mutex mu;
     static std::vector<std::pair<const void*, size_t>> limit;
-    if (bytes <= 48 * 1024) return MERA_OK;
     std::lock_guard<std::mutex> lock(mu);
     auto it = std::find_if(limit.begin(), limit.end(), [&](const std::pair<const void*, size_t>& e) { return e.first == fn; });
     if (it != limit.end() && it->second >= bytes) return MERA_OK;
@@ -1797,7 +1798,8 @@ int fused_launch(const FusedPlan<V>& plan, size_t i, PassArgs<V>& A, unsigned ny
                 h.hrun[o] = (unsigned char)(m | (len << 4));
                 o += len;
             }
-        const void* fn = tile_fn_hpass(plan.eng[i], plan.eng[i] == ENG_Q && !A.q_in ? 1 : 0);
+        const void* fn = tile_fn_hpass(plan.eng[i], plan.eng[i] == ENG_Q && !A.q_in ? 1 : 0,
+                                       plan.eng[i] == ENG_Q && A.q_out ? 1 : 0);
         const size_t hsm = ((size_t)1 << K) * sizeof(V);
         MERA_TRY(opt_in_smem(fn, hsm));
         void* args[] = {reinterpret_cast<void*>(&A), &h};

@@ -1128,7 +1128,10 @@ __device__ __forceinline__ void op_hmask(V (&x)[FRA], int m) {
     if (m & 8) op_h<V, 3>(x);
 }
 
-template <int ENG, int QIN>
+// QOUT (ENG_Q): 1 = the pass writes the fixed-point format, 0 = doubles
+// (the last pass of a run); a separate instantiation keeps the conversion
+// out of the instruction stream of the other passes.
+template <int ENG, int QIN, int QOUT>
 __global__ void __launch_bounds__(HP_THREADS, HP_CTAS_PER_SM)
     k_hpass(const __grid_constant__ PassArgs<double2> a, const __grid_constant__ HPassArgs h) {
     static_assert(ENG == ENG_I64 || ENG == ENG_Q, "int64 engines only");
@@ -1353,7 +1356,7 @@ __global__ void __launch_bounds__(HP_THREADS, HP_CTAS_PER_SM)
                         vx = (long long)((unsigned long long)vx << (-k));
                         vy = (long long)((unsigned long long)vy << (-k));
                     }
-                    if (a.q_out) {
+                    if constexpr (QOUT == 1) {
                         x[j].x = vx;
                         x[j].y = vy;
                     } else {

@@ -13,7 +13,7 @@ const void* tile_fn_q(int feat, int qin);
 const void* tile_fn_dpass();
 const void* tile_fn_i64(int feat, int qin);
 // the pipelined kernel of Hadamard / sign-term passes (ENG_I64 or ENG_Q)
-const void* tile_fn_hpass(int eng, int qin);
+const void* tile_fn_hpass(int eng, int qin, int qout);
 const void* tile_fn_fp(int feat, int qin);
 // the complex64 kernel
 const void* tile_fn_c64();
