@@ -1799,7 +1799,8 @@ int fused_launch(const FusedPlan<V>& plan, size_t i, PassArgs<V>& A, unsigned ny
                 o += len;
             }
         const void* fn = tile_fn_hpass(plan.eng[i], plan.eng[i] == ENG_Q && !A.q_in ? 1 : 0,
-                                       plan.eng[i] == ENG_Q && A.q_out ? 1 : 0);
+                                       plan.eng[i] == ENG_Q && A.q_out ? 1 : 0,
+                                       plan.eng[i] == ENG_Q ? (A.qend & 1) : 1);
         const size_t hsm = ((size_t)1 << K) * sizeof(V);
         MERA_TRY(opt_in_smem(fn, hsm));
         void* args[] = {reinterpret_cast<void*>(&A), &h};

@@ -1129,9 +1129,10 @@ __device__ __forceinline__ void op_hmask(V (&x)[FRA], int m) {
 }
 
 // QOUT (ENG_Q): 1 = the pass writes the fixed-point format, 0 = doubles
-// (the last pass of a run); a separate instantiation keeps the conversion
-// out of the instruction stream of the other passes.
-template <int ENG, int QIN, int QOUT>
+// (the last pass of a run); ODD (ENG_Q): 0 = the pass's level count to
+// scale away is even (no 1/sqrt(2) product).  Separate instantiations keep
+// code a pass never runs out of its instruction stream.
+template <int ENG, int QIN, int QOUT, int ODD>
 __global__ void __launch_bounds__(HP_THREADS, HP_CTAS_PER_SM)
     k_hpass(const __grid_constant__ PassArgs<double2> a, const __grid_constant__ HPassArgs h) {
     static_assert(ENG == ENG_I64 || ENG == ENG_Q, "int64 engines only");
@@ -1336,7 +1337,7 @@ __global__ void __launch_bounds__(HP_THREADS, HP_CTAS_PER_SM)
                 // format: one dithered (or nearest) shift, times 1/sqrt(2)
                 // for odd qend; then doubles unless the state stays fixed point
                 const int k = (a.qend >> 1) + (a.q_out ? a.qgo - a.qgi : 0);
-                const bool odd = a.qend & 1;
+                const bool odd = ODD && (a.qend & 1);
                 const int r2h = 759250124, r2l = 2134625280;   // round(2^61 / sqrt(2)) = r2h * 2^31 + r2l
                 const uint32_t t = dither ? hp_hash(gb, h.salt) : 0u;
 #pragma unroll
@@ -1344,10 +1345,12 @@ __global__ void __launch_bounds__(HP_THREADS, HP_CTAS_PER_SM)
                     long long vx = x[j].x, vy = x[j].y;
                     unsigned dr, di;
                     hp_dj(t, j, dither, dr, di);
-                    if (odd) {
-                        vx = hp_qmul_real(vx, r2h, r2l, dr);
-                        vy = hp_qmul_real(vy, r2h, r2l, di);
-                        hp_dj(t ^ 0x5BD1E995u, j, dither, dr, di);
+                    if constexpr (ODD == 1) {
+                        if (odd) {
+                            vx = hp_qmul_real(vx, r2h, r2l, dr);
+                            vy = hp_qmul_real(vy, r2h, r2l, di);
+                            hp_dj(t ^ 0x5BD1E995u, j, dither, dr, di);
+                        }
                     }
                     if (k > 0) {
                         vx = shr_lt32(vx + dk_lt32(dr, k), k);

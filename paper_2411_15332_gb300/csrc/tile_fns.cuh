@@ -1,5 +1,6 @@
 // Entry points of the tile-kernel variants (one translation unit per
-// engine: tile_q.cu, tile_i64.cu, tile_fp.cu).
+// engine: tile_q.cu, tile_i64.cu, tile_fp.cu; the Hadamard-pass kernel in
+// tile_h.cu).
 #pragma once
 
 #include "tile.cuh"
@@ -12,8 +13,10 @@ const void* tile_fn_q(int feat, int qin);
 // the streaming kernel of single-phase table passes (resident engine)
 const void* tile_fn_dpass();
 const void* tile_fn_i64(int feat, int qin);
-// the pipelined kernel of Hadamard / sign-term passes (ENG_I64 or ENG_Q)
-const void* tile_fn_hpass(int eng, int qin, int qout);
+// the Hadamard-pass kernel (ENG_I64 or ENG_Q): qin / qout = 1 when the pass
+// reads / writes doubles resp. fixed point (ENG_Q), odd = 1 when its level
+// count to scale away may be odd
+const void* tile_fn_hpass(int eng, int qin, int qout, int odd);
 const void* tile_fn_fp(int feat, int qin);
 // the complex64 kernel
 const void* tile_fn_c64();

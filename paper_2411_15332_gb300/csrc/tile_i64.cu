@@ -14,12 +14,4 @@ const void* tile_fn_i64(int feat, int qin) {
     }
 }
 
-const void* tile_fn_hpass(int eng, int qin, int qout) {
-    if (eng == ENG_Q) {
-        if (qin) return qout ? (const void*)k_hpass<ENG_Q, 1, 1> : (const void*)k_hpass<ENG_Q, 1, 0>;
-        return qout ? (const void*)k_hpass<ENG_Q, 0, 1> : (const void*)k_hpass<ENG_Q, 0, 0>;
-    }
-    return (const void*)k_hpass<ENG_I64, 0, 0>;
-}
-
 }  // namespace mera
