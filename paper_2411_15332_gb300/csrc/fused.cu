@@ -2012,6 +2012,13 @@ static int describe_fused(int n, int dtype, const std::vector<PrepOp>& ops, std:
             if (A.ops[o].type == TOP_Z4) nterms += A.ops[o].aux2;
         dsep += " z4_terms=" + std::to_string(nterms) + (plan.dpass[i] ? " stream" : "") +
                 (plan.hpass[i] ? " pipelined" : "") + (A.gather ? " gather" : "") + (A.scatter ? " scatter" : "");
+        if (plan.eng[i] == ENG_Q) {
+            // resident scaling: levels scaled at phase exits (2 * shift) and at the end
+            int exits = 0;
+            for (int ph = 0; ph < A.nph; ++ph) exits += 2 * A.ph[ph].qsh;
+            dsep += " qend=" + std::to_string(A.qend) + " qexit=" + std::to_string(exits) + " qgi=" +
+                    std::to_string(A.qgi);
+        }
         dsep += " phase_ops=[";
         for (int ph = 0; ph < A.nph; ++ph)
             dsep += std::to_string(A.ph[ph].op_end - A.ph[ph].op_begin) + (A.ph[ph].permuted ? "p" : "") +

@@ -28,6 +28,7 @@ def parse(summary):
             passes.append({"single": True})
             continue
         d = dict(re.findall(r"(\w+)=([\w\d]+)", line.split("tile=")[0]))
+        d.update(re.findall(r"\b(qend|qexit|qgi)=(\d+)", line))
         d["phase_ops"] = re.search(r"phase_ops=\[([^\]]*)\]", line).group(1)
         passes.append(d)
     return {k: int(v) for k, v in info.items()}, passes
@@ -121,3 +122,32 @@ def test_dithered_plan_split_by_a_per_gate_op(core):
     assert sum(1 for p in passes if p.get("single")) == 1
     tile = [l for l in summary.splitlines()[1:] if "per-gate" not in l]
     assert tile and all("pipelined" in l for l in tile)
+
+
+@pytest.mark.parametrize("n,iters", [(33, 8), (20, 3), (13, 2)])
+def test_dithered_scaling_takes_every_level_once(core, n, iters):
+    """Resident scaling in a dithered plan: no scaling at phase exits; a
+    pass inside a run scales an even number of levels (an odd count leaves
+    sqrt(2) for the next pass); the run's last pass takes what is left, so
+    over the circuit every butterfly level is scaled exactly once."""
+    ops, _ = inputs.grover_circuit(n, iters, seed=3)
+    head, passes = parse(core.plan_summary(n, ops))
+    assert head["dither"] == 1
+    assert all(int(p["qexit"]) == 0 for p in passes)
+    assert all(int(p["qend"]) % 2 == 0 for p in passes[:-1])
+    assert sum(int(p["qend"]) for p in passes) == sum(int(p["nh"]) for p in passes) == n * (2 * iters + 1)
+    # headroom: every level pending at once, the carried factor included
+    pend = 0
+    for p in passes:
+        tot = int(p["nh"]) + pend
+        assert int(p["qgi"]) == (tot + 1) // 2 + 2
+        pend = tot - int(p["qend"])
+
+
+def test_resident_scaling_without_dither_uses_exits(core):
+    """Without dither (the layered circuit) a pass scales at phase exits once
+    8 levels are pending and the rest at its end; every level once."""
+    head, passes = parse(core.plan_summary(30, inputs.layered_circuit(30, 20, seed=2)))
+    assert head["dither"] == 0
+    assert sum(int(p["qend"]) + int(p["qexit"]) for p in passes) == sum(int(p["nh"]) for p in passes) == 30
+    assert any(int(p["qexit"]) > 0 for p in passes)
