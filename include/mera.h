@@ -167,10 +167,16 @@ int mera_apply_matrix(mera_state* s, const double* matrix, const int* targets, i
 int mera_apply_circuit(mera_state* s, const mera_op* ops, size_t nops, int mode);
 
 /* Describe how MERA_MODE_FUSED would run ops[0..nops-1] on n qubits of
- * `dtype`, without touching a GPU: one line per tile pass (tile bits,
- * arithmetic engine, Hadamard levels, register phases, op kinds), written
- * as a NUL-terminated string into out[cap] (truncated if longer).  Host
- * only; *npasses (may be NULL) receives the number of passes. */
+ * `dtype`, without touching a GPU: a header line (tile bits, passes,
+ * whether the complex128 state stays int64 fixed point across passes and
+ * whether its roundings are dithered), then one line per tile pass (tile
+ * bits, arithmetic engine, Hadamard levels, register phases, op kinds,
+ * the kernel that runs it: "stream" / "pipelined" (Hadamard-pass kernel) /
+ * neither (general tile kernel), permutation runs on its loads / stores
+ * ("gather" / "scatter"), and for the resident engine its scaling: levels
+ * scaled at the end and at phase exits, headroom bits), written as a
+ * NUL-terminated string into out[cap] (truncated if longer).  Host only;
+ * *npasses (may be NULL) receives the number of passes. */
 int mera_plan_summary(int n, int dtype, const mera_op* ops, size_t nops, char* out, size_t cap, int* npasses);
 
 /* H on every qubit q with bit q of `mask` set: the RH structure of Sec.
