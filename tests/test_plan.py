@@ -151,3 +151,32 @@ def test_resident_scaling_without_dither_uses_exits(core):
     assert head["dither"] == 0
     assert sum(int(p["qend"]) + int(p["qexit"]) for p in passes) == sum(int(p["nh"]) for p in passes) == 30
     assert any(int(p["qexit"]) > 0 for p in passes)
+
+
+def test_hadamard_kernel_eligibility(core):
+    """Which passes the Hadamard-pass kernel runs: butterflies and exact
+    sign terms only (no tables), a closing permutation run on the stores
+    allowed; in a circuit that keeps double storage its per-tile int64
+    engine takes the Hadamard passes."""
+    n = 20
+    rng = np.random.default_rng(5)
+    ops = inputs.hadamard_all(n)
+    ops += [op("Z", (q,)) for q in range(0, n, 3)]
+    ops += [op("RZ", (q,), (), (float(t),)) for q, t in enumerate(rng.uniform(0, 6.28, n))]
+    ops += inputs.hadamard_all(n)
+    summary = core.plan_summary(n, ops)
+    head, passes = parse(summary)
+    lines = summary.splitlines()[1:]
+    assert head["resident"] == 0
+    for p, line in zip(passes, lines):
+        has_table = int(re.search(r"dsep=(\d+)", line).group(1)) > 0
+        if "pipelined" in line:
+            assert p["eng"] == "i64" and not has_table and p["load_smem"] == "1"
+        if has_table:
+            assert "pipelined" not in line
+    assert any("pipelined" in l for l in lines)
+    # the layered circuit: its three Hadamard passes carry the CNOT run after
+    # them on scattered stores and still run in the kernel
+    summary = core.plan_summary(30, inputs.layered_circuit(30, 20, seed=2)).splitlines()[1:]
+    hp = [l for l in summary if "pipelined" in l]
+    assert len(hp) == 3 and all("scatter" in l and "gather" not in l for l in hp)
