@@ -185,6 +185,31 @@ int mera_plan_summary(int n, int dtype, const mera_op* ops, size_t nops, char* o
  * result as the RH-MVM of Algorithm 1 for mask = all qubits. */
 int mera_hadamard_layer(mera_state* s, uint64_t mask);
 
+/* The paper's own RH-MVM of H^{(x)n} (Sec. III-B.2, Table II, Algorithm 1):
+ * out = H^{(x)n} in, out of place, with the signs of the matrix elements
+ * parsed on demand by the quadrant recursion of Fig. 3 (O(n) each) under one
+ * of four sign-computation methods:
+ *   MERA_RH_NONOPT   every element's sign             (2^n * 2^n signs)
+ *   MERA_RH_QUARTER  Method 1, the upper-left quarter  (2^(n-1) * 2^(n-1))
+ *   MERA_RH_BLOCK    Method 2, first block + one sign per other block of
+ *                    `block` columns (0 = sqrt(2^(n-1)) rounded down to a
+ *                    power of two, Theorem 3)     (2^(n-1) (2^(n-1)/b + b - 1))
+ *   MERA_RH_LOG      Method 3 / Algorithm 1, signs at columns 2^p only
+ *                                                   (2^(n-1) * (n - 1))
+ * in and out: distinct complex128 states of the same n, 2 <= n <= 18 (the
+ * method keeps a row's signs as bits in shared memory); `block` must be a
+ * power of two <= min(256, 2^(n-1)) with 2^(n-1)/block <= 512.  Uses the
+ * scratch memory of `out` (16 * 2^n + 256 bytes).  The MVM is O(4^n) work:
+ * H^{(x)n} on a state is mera_hadamard_layer (butterflies, O(n 2^n)); these
+ * calls exist to run the paper's methods as written.  Runs on out's stream
+ * after in's queued work; with sign_count non-NULL, waits for the result
+ * and stores the number of compute_sign evaluations (Table II). */
+#define MERA_RH_NONOPT 0
+#define MERA_RH_QUARTER 1
+#define MERA_RH_BLOCK 2
+#define MERA_RH_LOG 3
+int mera_rh_mvm(mera_state* in, mera_state* out, int method, int block, uint64_t* sign_count);
+
 /* ---- readouts (Sec. II-A Eq. 4-5); synchronous, float64 accumulation -- */
 
 /* sum_i |a_i|^2 */
@@ -311,13 +336,19 @@ int mera_adjoint_grad(mera_batch* b, int nslots, int L, const double* theta, dou
 
 /* ---- kernel timing ------------------------------------------------------ */
 
-/* Kernel classes timed when profiling is on. */
-#define MERA_KCLASS_GATE 0      /* per-gate kernels */
-#define MERA_KCLASS_TILE 1      /* fused tile-pass kernel */
+/* Kernel classes timed when profiling is on (one class per kernel family,
+ * so that a workload's dominant kernel can be told apart). */
+#define MERA_KCLASS_GATE 0      /* per-gate kernels not listed below (two- and three-target) */
+#define MERA_KCLASS_TILE 1      /* general fused tile-pass kernel */
 #define MERA_KCLASS_REDUCE 2    /* reductions */
 #define MERA_KCLASS_DAX 3       /* DAX / DAS MTP and MVM kernels */
 #define MERA_KCLASS_QNN 4       /* batched QNN / adjoint kernels */
-#define MERA_KCLASS_COUNT 5
+#define MERA_KCLASS_HPASS 5     /* Hadamard-pass kernel (butterflies and sign terms) */
+#define MERA_KCLASS_DPASS 6     /* streaming single-phase table-pass kernel */
+#define MERA_KCLASS_GATE_DIAG 7 /* per-gate diagonal kernels (phases, sign flips) */
+#define MERA_KCLASS_GATE_1Q 8   /* per-gate one-target kernels (2x2 and swaps with phases) */
+#define MERA_KCLASS_RH 9        /* the paper's RH sign-method MVM kernels */
+#define MERA_KCLASS_COUNT 10
 
 /* Turn CUDA-event timing of every launch on/off (process-wide) and clear
  * the accumulated figures. */

@@ -6,11 +6,13 @@ resolved lazily so that ``paper_2411_15332_gb300.inputs`` (the seeded
 workload generators) imports without touching the CUDA library.
 """
 
-__all__ = ["State", "DAX", "DAS", "Batch", "AdjointExpectation", "gate_matrix", "launch_count", "profile_enable", "profile_read", "plan_summary"]
+__all__ = ["State", "DAX", "DAS", "Batch", "AdjointExpectation", "gate_matrix", "launch_count", "profile_enable",
+           "profile_read", "plan_summary", "rh_mvm", "RH_METHODS"]
 
 
 def __getattr__(name):
-    if name in ("State", "gate_matrix", "launch_count", "profile_enable", "profile_read", "plan_summary"):
+    if name in ("State", "gate_matrix", "launch_count", "profile_enable", "profile_read", "plan_summary", "rh_mvm",
+                "RH_METHODS"):
         from . import core
         return getattr(core, name)
     if name in ("Batch", "AdjointExpectation"):

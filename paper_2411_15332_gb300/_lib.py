@@ -17,9 +17,10 @@ LIB_PATH = os.path.join(PKG, "_build", "libmera.so")
 MERA_OK, MERA_EINVAL, MERA_ENOMEM, MERA_EUNSUPPORTED, MERA_ECUDA, MERA_ETIMEOUT = range(6)
 MERA_C64, MERA_C128 = 0, 1
 MODE_PER_GATE, MODE_FUSED = 0, 1
-KCLASS_GATE, KCLASS_TILE, KCLASS_REDUCE, KCLASS_DAX, KCLASS_QNN = range(5)
-KCLASS_COUNT = 5
-KCLASS_NAMES = ("gate", "tile", "reduce", "dax", "qnn")
+(KCLASS_GATE, KCLASS_TILE, KCLASS_REDUCE, KCLASS_DAX, KCLASS_QNN, KCLASS_HPASS, KCLASS_DPASS,
+ KCLASS_GATE_DIAG, KCLASS_GATE_1Q, KCLASS_RH) = range(10)
+KCLASS_COUNT = 10
+KCLASS_NAMES = ("gate", "tile", "reduce", "dax", "qnn", "hpass", "dpass", "gate_diag", "gate_1q", "rh")
 
 GATES = ["I", "X", "Y", "Z", "H", "S", "SDG", "T", "TDG", "SX", "SXDG", "P", "RX", "RY", "RZ",
          "R", "U2", "U", "SWAP", "ISWAP", "DCX", "ECR", "RXX", "RYY", "RZZ", "RZX", "FLIP", "MATRIX"]
@@ -105,6 +106,7 @@ PROTOS = {
     "mera_batch_forward": (I, [P, I, I, DP]),
     "mera_batch_observables": (I, [P, IP, I, I, DP]),
     "mera_adjoint_grad": (I, [P, I, I, DP, DP, DP]),
+    "mera_rh_mvm": (I, [P, P, I, I, U64P]),
     "mera_profile_enable": (I, [I]),
     "mera_profile_read": (I, [U64P, DP, DP]),
 }

@@ -184,6 +184,18 @@ def plan_summary(n: int, ops, dtype: str = "c128") -> str:
     return buf.value.decode()
 
 
+RH_METHODS = ("nonopt", "quarter", "block", "log")
+
+
+def rh_mvm(src: State, dst: State, method: str = "log", block: int = 0) -> int:
+    """The paper's RH-MVM dst = H^(x)n src (Sec. III-B.2, Algorithm 1) with
+    one of its four sign methods (RH_METHODS); returns the number of sign
+    computations (Table II).  Out of place, complex128, 2 <= n <= 18."""
+    cnt = C.c_uint64()
+    L.check(L.lib().mera_rh_mvm(src.handle, dst.handle, RH_METHODS.index(method), int(block), C.byref(cnt)))
+    return int(cnt.value)
+
+
 def launch_count() -> int:
     return int(L.lib().mera_launch_count())
 

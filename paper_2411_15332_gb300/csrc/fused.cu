@@ -1502,6 +1502,10 @@ int fused_build(int n, const std::vector<PrepOp>& ops, FusedPlan<V>& plan, bool 
     plan.qguard = 0;
     plan.dither = false;
     bool mixed = false;
+    // MERA_RESIDENT=0 keeps complex128 states in float64 between passes
+    // (per-tile int64 inside Hadamard passes)
+    if (const char* e = getenv("MERA_RESIDENT"))
+        if (atoi(e) == 0) resident_ok = false;
     if (sizeof(V) == 16 && !fp_only && resident_ok) {
         // unitary gates only (the norm bounds every amplitude) and some
         // arithmetic.  Where every mixing (non-monomial) gate precedes the
@@ -1727,7 +1731,7 @@ int fused_launch(const FusedPlan<V>& plan, size_t i, PassArgs<V>& A, unsigned ny
     const uint64_t tiles = 1ull << (plan.n - K);
     MERA_RETURN_IF(tiles > 0x7fffffffull, MERA_EUNSUPPORTED, "too many tiles");
     MERA_RETURN_IF(ny == 0 || ny > 65535, MERA_EUNSUPPORTED, "batch of %u states per launch", ny);
-    launch_begin(st, MERA_KCLASS_TILE, 2.0 * (double)(1ull << plan.n) * sizeof(V) * ny);
+    const double pass_bytes = 2.0 * (double)(1ull << plan.n) * sizeof(V) * ny;
     if (sizeof(V) == 16 && ny == 1 && plan.dpass[i]) {
         DPassArgs d = plan.dargs[i];
         d.psi = reinterpret_cast<double2*>(A.psi);
@@ -1739,6 +1743,7 @@ int fused_launch(const FusedPlan<V>& plan, size_t i, PassArgs<V>& A, unsigned ny
         if (!sms) MERA_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0));
         const uint64_t ctas = std::max<uint64_t>(1, std::min<uint64_t>(tiles, 16ull * (uint64_t)sms));
         void* args[] = {&d};
+        launch_begin(st, MERA_KCLASS_DPASS, pass_bytes);
         MERA_CHECK_CUDA(cudaLaunchKernel(tile_fn_dpass(), dim3((unsigned)ctas, 1), dim3(2u << (K - FR)), args, 0, st));
         return launch_end(st);
     }
@@ -1804,9 +1809,11 @@ int fused_launch(const FusedPlan<V>& plan, size_t i, PassArgs<V>& A, unsigned ny
         const size_t hsm = ((size_t)1 << K) * sizeof(V);
         MERA_TRY(opt_in_smem(fn, hsm));
         void* args[] = {reinterpret_cast<void*>(&A), &h};
+        launch_begin(st, MERA_KCLASS_HPASS, pass_bytes);
         MERA_CHECK_CUDA(cudaLaunchKernel(fn, dim3(ctas), dim3(1u << (K - FR)), args, hsm, st));
         return launch_end(st);
     }
+    launch_begin(st, MERA_KCLASS_TILE, pass_bytes);
     MERA_TRY(launch_tile<V>(plan.eng[i], plan.feat[i], dim3((unsigned)tiles, ny), 1u << (K - FR), smem, st, A));
     return launch_end(st);
 }

@@ -292,7 +292,7 @@ static int launch_prepared(mera_state* s, const PrepOp& P) {
             fill_common(s, P, false, a);
             a.v[0] = to_v<V>(P.v[0]);
             a.code[0] = phase_code(P.v[0]);
-            launch_begin(s->stream, MERA_KCLASS_GATE, 2.0 * eb * (double)a.count);
+            launch_begin(s->stream, MERA_KCLASS_GATE_DIAG, 2.0 * eb * (double)a.count);
             k_phase<V><<<grid_for(a.count, threads), threads, 0, s->stream>>>(a);
             return launch_end(s->stream);
         }
@@ -307,7 +307,7 @@ static int launch_prepared(mera_state* s, const PrepOp& P) {
         }
         int nact = 0;
         for (int r = 0; r < (1 << P.k); ++r) nact += a.flag[r];
-        launch_begin(s->stream, MERA_KCLASS_GATE,
+        launch_begin(s->stream, MERA_KCLASS_GATE_DIAG,
                      2.0 * eb * (double)a.count * nact / (double)(1 << P.k));
         k_diag<V><<<grid_for(a.count, threads), threads, 0, s->stream>>>(a);
         return launch_end(s->stream);
@@ -328,13 +328,13 @@ static int launch_prepared(mera_state* s, const PrepOp& P) {
         if (qc < 5 && ncnt >= 32) {
             fill_common(s, P, false, a);
             a.qc = qc;
-            launch_begin(s->stream, MERA_KCLASS_GATE, 2.0 * eb * (double)a.count);
+            launch_begin(s->stream, MERA_KCLASS_GATE_1Q, 2.0 * eb * (double)a.count);
             if (mono) k_dense1_shfl<V, true><<<grid_for(a.count, threads), threads, 0, s->stream>>>(a);
             else k_dense1_shfl<V, false><<<grid_for(a.count, threads), threads, 0, s->stream>>>(a);
             return launch_end(s->stream);
         }
         fill_common(s, P, true, a);
-        launch_begin(s->stream, MERA_KCLASS_GATE, 4.0 * eb * (double)a.count);
+        launch_begin(s->stream, MERA_KCLASS_GATE_1Q, 4.0 * eb * (double)a.count);
         if (mono) k_dense1_pair<V, true><<<grid_for(a.count, threads), threads, 0, s->stream>>>(a);
         else k_dense1_pair<V, false><<<grid_for(a.count, threads), threads, 0, s->stream>>>(a);
         return launch_end(s->stream);

@@ -84,12 +84,29 @@ class Server:
     def used_bytes(self) -> int:
         return sum(self._group_bytes(g.n, g.capacity) for g in self.groups.values())
 
+    def _release_idle(self, keep: int) -> bool:
+        """Free the batches of groups with no active slot (other than qubit
+        count ``keep``), so that their memory can go to a qubit count that
+        does not fit; returns whether anything was freed."""
+        idle = [m for m, g in self.groups.items() if m != keep and not g.active]
+        for m in idle:
+            g = self.groups.pop(m)
+            close = getattr(g.batch, "close", None)
+            if close is not None:
+                close()
+        return bool(idle)
+
     def _group(self, n: int) -> Optional[_Group]:
         g = self.groups.get(n)
         if g is not None:
             return g
         per_slot = self._group_bytes(n, 1)
         room = (self.mem_budget - self.used_bytes()) // per_slot
+        want = min(self.slots_per_n, self.mem_budget // per_slot)
+        if room < want and self._release_idle(n):
+            # groups sized for earlier qubit counts would otherwise hold the
+            # budget forever: idle ones give their memory back
+            room = (self.mem_budget - self.used_bytes()) // per_slot
         cap = int(min(self.slots_per_n, room))
         if cap < 1:
             return None
@@ -170,25 +187,27 @@ class Server:
     def active(self) -> int:
         return sum(len(g.active) for g in self.groups.values())
 
-    def run(self, requests: List[Request], rate: Optional[float] = None, timeout: float = 600.0):
-        """Serve ``requests``; with ``rate`` their ``arrival`` offsets are
-        honoured against the server clock (Poisson arrivals), else all
-        arrive at once.  Returns the finished requests."""
+    def run(self, requests: List[Request], timeout: float = 600.0):
+        """Serve ``requests``: each is submitted once the server clock
+        (seconds since this call) reaches its ``arrival`` offset (all at
+        once when every offset is 0).  Returns the requests of this call,
+        finished, in completion order."""
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
         self.t0 = self.clock()
         total = len(pending)
-        while len(self.finished) < total:
+        base = len(self.finished)
+        while len(self.finished) - base < total:
             now = self.now()
             if now > timeout:
                 raise TimeoutError(f"serving did not finish in {timeout} s")
-            while pending and (rate is None or pending[0].arrival <= now):
+            while pending and pending[0].arrival <= now:
                 self.submit(pending.popleft())
             if not self.queue and not self.active():
                 if pending:
                     time.sleep(max(0.0, min(0.001, pending[0].arrival - now)))
                 continue
             self.tick()
-        return self.finished
+        return self.finished[base:]
 
     def stats(self) -> dict:
         lat = np.array([r.latency for r in self.finished if r.error is None and r.latency is not None])

@@ -1,7 +1,16 @@
 """Helpers shared by the GPU parity tests."""
 import numpy as np
 
+# max |d amp| against the FP64 oracle, per state dtype
 TOL = {"c128": 1e-12, "c64": 2e-5}
+
+
+def obs_tol(dtype, onorm):
+    """Bound for a quantity read from a state whose amplitudes meet TOL: an
+    expectation <psi|O|psi> or an adjoint derivative 2 Re <lambda|dU|psi>
+    with observable O of operator norm ``onorm`` (1 for Z_q, n for
+    sum_q Z_q) is held to onorm * TOL[dtype]."""
+    return onorm * TOL[dtype]
 
 
 def lib_ready():

@@ -111,7 +111,7 @@ def test_mvm(dtype, kind):
     dst = new_state(nq, dtype)
     dev.mvm(src, dst)
     ref = odx.dax_mvm(odx.dax_encode(M), psi)
-    assert max_err(dst.to_numpy(), ref) <= TOL[dtype] * 8
+    assert max_err(dst.to_numpy(), ref) <= TOL[dtype]
 
 
 def test_mvm_large_monomial_layer():

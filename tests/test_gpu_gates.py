@@ -77,7 +77,7 @@ def test_catalogue_random_controls(n, dtype, mode):
     s = new_state(n, dtype, psi0)
     s.apply_circuit(ops, mode=mode)
     ref = sv.simulate(n, ops, psi0)
-    assert max_err(s.to_numpy(), ref) <= TOL[dtype] * 4
+    assert max_err(s.to_numpy(), ref) <= TOL[dtype]
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
@@ -88,7 +88,7 @@ def test_long_fused_circuit_many_tiles(dtype):
     s = new_state(n, dtype, psi0)
     s.apply_circuit(ops, mode="fused")
     ref = sv.simulate(n, ops, psi0)
-    assert max_err(s.to_numpy(), ref) <= TOL[dtype] * 4
+    assert max_err(s.to_numpy(), ref) <= TOL[dtype]
 
 
 @pytest.mark.parametrize("k", [1, 2, 3])
@@ -104,7 +104,7 @@ def test_matrix_gate(k, dtype):
         qs = rng.choice(n, size=k + 1, replace=False)
         s.apply_matrix(U, list(qs[1:]), [int(qs[0])])
         sv.apply_matrix(ref, n, U, list(qs[1:]), [int(qs[0])])
-    assert max_err(s.to_numpy(), ref) <= TOL[dtype] * 4
+    assert max_err(s.to_numpy(), ref) <= TOL[dtype]
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
@@ -137,7 +137,7 @@ def test_hadamard_layer(n, dtype):
         for q in range(n):
             if (mask >> q) & 1:
                 sv.apply_op(ref, n, ("H", (q,), (), (), 0))
-        assert max_err(s.to_numpy(), ref) <= TOL[dtype] * 4
+        assert max_err(s.to_numpy(), ref) <= TOL[dtype]
 
 
 def test_hadamard_all_uniform():

@@ -7,7 +7,7 @@ import pytest
 from oracle import circuits as oc
 from oracle import statevector as sv
 from paper_2411_15332_gb300 import inputs
-from tests.gpu_helpers import TOL, lib_ready, max_err
+from tests.gpu_helpers import TOL, lib_ready, max_err, obs_tol
 
 pytestmark = pytest.mark.gpu
 
@@ -32,10 +32,10 @@ def test_batch_forward_matches_oracle(dtype, n, L, B):
     obs = b.observables(range(B), q=0)
     for j in range(B):
         ref = sv.simulate(n, inputs.ansatz_ops(n, theta[j]))
-        assert max_err(got[j], ref) <= TOL[dtype] * 4
-        assert abs(obs[j, 0] - 1.0) <= (1e-12 if dtype == "c128" else 1e-5)
-        assert abs(obs[j, 1] - sv.expect_z(ref, n, 0)) <= (1e-12 if dtype == "c128" else 2e-5)
-        assert abs(obs[j, 2] - sv.expect_z_sum(ref, n)) <= (1e-11 if dtype == "c128" else 2e-4)
+        assert max_err(got[j], ref) <= TOL[dtype]
+        assert abs(obs[j, 0] - 1.0) <= TOL[dtype]
+        assert abs(obs[j, 1] - sv.expect_z(ref, n, 0)) <= obs_tol(dtype, 1)
+        assert abs(obs[j, 2] - sv.expect_z_sum(ref, n)) <= obs_tol(dtype, n)
 
 
 def test_slot_results_do_not_depend_on_the_mix():
@@ -64,40 +64,56 @@ def test_slot_results_do_not_depend_on_the_mix():
     assert np.array_equal(mix.observables([5], 0)[0], ref_obs)
 
 
-@pytest.mark.parametrize("dtype,tol", [("c128", 1e-10), ("c64", 5e-4)])
-def test_adjoint_matches_parameter_shift_and_fd(dtype, tol):
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_adjoint_matches_parameter_shift_and_fd(dtype):
     n, L, B = 6, 2, 3
+    tol = obs_tol(dtype, n)          # loss = sum_q <Z_q>: observable norm n
     theta = inputs.qnn_batch(B, n, L, seed=11)
     b = _batch(n, B, dtype)
     loss, grad = b.adjoint_grad(theta)
     for j in range(B):
         f = oc.qnn_value(n, theta[j], inputs.ansatz_ops, "zsum")
-        assert abs(loss[j] - f) <= (1e-11 if dtype == "c128" else 5e-4)
+        assert abs(loss[j] - f) <= tol
         ps = oc.param_shift_grad(n, theta[j], inputs.ansatz_ops, "zsum")
-        np.testing.assert_allclose(grad[j], ps, atol=tol)
+        np.testing.assert_allclose(grad[j], ps, atol=tol, rtol=0)
+    # central differences carry O(h^2) ~ 1e-12 truncation and ~1e-10
+    # cancellation error of their own
     fd = oc.finite_diff_grad(n, theta[0], inputs.ansatz_ops, "zsum")
-    np.testing.assert_allclose(grad[0], fd, atol=max(tol, 1e-8))
+    np.testing.assert_allclose(grad[0], fd, atol=max(tol, 1e-8), rtol=0)
 
 
-def test_adjoint_training_shape_sampled_params():
-    """The training workload's shape (n = 16, 10 layers, 320 angles) on a
-    few circuits; every angle of circuit 0 is checked against the oracle's
-    parameter shift for a sample of 12 parameters."""
-    n, L, B = 16, 10, 4
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_adjoint_training_full_shape(dtype):
+    """The training workload at its full shape (1024 circuits, n = 16, 10
+    layers, 320 angles each) in one call; every one of the 320 derivatives
+    and the loss of three circuits (first, middle, last row) against the
+    oracle's reverse sweep, and 8 derivatives of circuit 0 against the
+    parameter-shift rule."""
+    n, L, B = 16, 10, 1024
+    tol = obs_tol(dtype, n)
     theta = inputs.qnn_batch(B, n, L, seed=5)
-    b = _batch(n, B, "c128")
+    b = _batch(n, B, dtype)
     loss, grad = b.adjoint_grad(theta)
+    b.close()
+    ops_fn = inputs.ansatz_ops
+    worst_g, worst_f = 0.0, 0.0
+    for j in (0, B // 2, B - 1):
+        f, g = oc.adjoint_grad(n, theta[j], ops_fn, "zsum")
+        worst_g = max(worst_g, float(np.max(np.abs(grad[j] - g))))
+        worst_f = max(worst_f, abs(loss[j] - f))
     rng = np.random.default_rng(0)
     flat = theta[0].reshape(-1)
-    ops_fn = inputs.ansatz_ops
-    for p in rng.choice(flat.size, size=12, replace=False):
+    for p in rng.choice(flat.size, size=8, replace=False):
         tp = flat.copy()
         tp[p] += np.pi / 2
         fp = oc.qnn_value(n, tp.reshape(theta[0].shape), ops_fn, "zsum")
         tp[p] -= np.pi
         fm = oc.qnn_value(n, tp.reshape(theta[0].shape), ops_fn, "zsum")
-        assert abs(grad[0].reshape(-1)[p] - 0.5 * (fp - fm)) <= 1e-9
-    assert abs(loss[0] - oc.qnn_value(n, theta[0], ops_fn, "zsum")) <= 1e-10
+        worst_g = max(worst_g, abs(grad[0].reshape(-1)[p] - 0.5 * (fp - fm)))
+    print(f"adjoint n=16 L=10 B=1024 {dtype}: max |d grad| = {worst_g:.3e}, max |d loss| = {worst_f:.3e} "
+          f"(bound {tol:.1e})")
+    assert worst_g <= tol
+    assert worst_f <= tol
 
 
 def test_autograd_function():
@@ -109,9 +125,9 @@ def test_autograd_function():
     loss = AdjointExpectation.apply(theta, b)
     loss.backward()
     ref = np.mean([oc.qnn_value(n, theta.detach().numpy()[j], inputs.ansatz_ops, "zsum") for j in range(B)])
-    assert abs(loss.item() - ref) <= 1e-11
+    assert abs(loss.item() - ref) <= obs_tol("c128", n)
     ps = np.stack([oc.param_shift_grad(n, theta.detach().numpy()[j], inputs.ansatz_ops, "zsum") for j in range(B)])
-    np.testing.assert_allclose(theta.grad.numpy(), ps / B, atol=1e-10)
+    np.testing.assert_allclose(theta.grad.numpy(), ps / B, atol=obs_tol("c128", n), rtol=0)
 
 
 def test_server_mix_equals_alone_and_oracle():

@@ -87,3 +87,52 @@ def test_param_shift_matches_fd_deeper():
         g = oc.param_shift_grad(n, theta, inputs.ansatz_ops, obs)
         fd = oc.finite_diff_grad(n, theta, inputs.ansatz_ops, obs)
         np.testing.assert_allclose(g, fd, atol=1e-8)
+
+
+def test_monomial_amplitudes_vectorised_equals_trace_and_simulation():
+    """The array form of the single-path trace gives the scalar trace's
+    value for every index, and the full simulation's."""
+    n = 10
+    ops = inputs.layered_circuit(n, 4, seed=2)
+    psi = sv.simulate(n, ops)
+    rng = np.random.default_rng(5)
+    idx = rng.integers(0, 1 << n, size=64)
+    init = lambda j: np.full(np.shape(j), 2.0 ** (-n / 2), dtype=complex)
+    got = oc.monomial_amplitudes(n, ops[n:], idx, init)
+    np.testing.assert_allclose(got, psi[idx], atol=1e-14, rtol=0)
+    for i, a in zip(idx[:8], got[:8]):
+        assert abs(a - oc.monomial_amplitude(n, ops[n:], int(i), lambda j: 2.0 ** (-n / 2))) <= 1e-16
+
+
+def test_monomial_amplitudes_rejects_dense():
+    with pytest.raises(ValueError):
+        oc.monomial_amplitudes(2, [inputs.op("H", (0,))], [0, 1], lambda j: np.ones(np.shape(j)))
+
+
+@pytest.mark.parametrize("n,L", [(2, 1), (3, 2), (5, 2)])
+@pytest.mark.parametrize("obs", ["zsum", "z0"])
+def test_adjoint_grad_matches_parameter_shift(n, L, obs):
+    """The reverse sweep gives the value and every derivative of the exact
+    parameter-shift rule (RY / RZ generators have eigenvalues +-1/2), and
+    agrees with central differences."""
+    theta = inputs.qnn_batch(1, n, L, seed=n * 10 + L)[0]
+    f, g = oc.adjoint_grad(n, theta, inputs.ansatz_ops, obs)
+    assert f == pytest.approx(oc.qnn_value(n, theta, inputs.ansatz_ops, obs), abs=1e-13)
+    ps = oc.param_shift_grad(n, theta, inputs.ansatz_ops, obs)
+    np.testing.assert_allclose(g, ps, atol=1e-12, rtol=0)
+    fd = oc.finite_diff_grad(n, theta, inputs.ansatz_ops, obs)
+    np.testing.assert_allclose(g, fd, atol=1e-8, rtol=0)
+
+
+def test_adjoint_grad_closed_form_n2():
+    """n = 2, one layer: f = cos(a1) + cos(a0) cos(a1) (derived in
+    test_qnn_single_qubit_closed_form), so df/da0 = -sin(a0) cos(a1),
+    df/da1 = -sin(a1) (1 + cos(a0)) and the RZ angles have zero gradient."""
+    rng = np.random.default_rng(4)
+    theta = rng.uniform(0, 2 * math.pi, size=(1, 2, 2))
+    f, g = oc.adjoint_grad(2, theta, inputs.ansatz_ops, "zsum")
+    a0, a1 = theta[0, 0, 0], theta[0, 0, 1]
+    assert f == pytest.approx(math.cos(a1) + math.cos(a0) * math.cos(a1), abs=1e-14)
+    assert g[0, 0, 0] == pytest.approx(-math.sin(a0) * math.cos(a1), abs=1e-14)
+    assert g[0, 0, 1] == pytest.approx(-math.sin(a1) * (1 + math.cos(a0)), abs=1e-14)
+    np.testing.assert_allclose(g[0, 1], 0.0, atol=1e-14)

@@ -89,3 +89,53 @@ def test_malformed_request_rejected():
     r = Request(rid=0, n=5, theta=np.zeros((2, 3, 5)))
     srv.submit(r)
     assert r.error is not None
+
+
+class FakeClock:
+    """Deterministic server clock: every reading advances it by ``dt``."""
+
+    def __init__(self, dt=2e-4):
+        self.t, self.dt = 0.0, dt
+
+    def __call__(self):
+        self.t += self.dt
+        return self.t
+
+
+def test_arrivals_are_honoured_and_latencies_non_negative():
+    """Poisson arrivals: no request is submitted, admitted or finished
+    before its arrival offset, every latency is >= 0, and the run lasts at
+    least as long as the arrival window (so the throughput cannot exceed
+    the offered rate over that window)."""
+    rate = 500.0
+    reqs = requests_from_workload(inputs.qnn_requests(40, seed=4, n_lo=5, n_hi=7, l_lo=2, l_hi=4), rate=rate)
+    window = max(r.arrival for r in reqs)
+    assert window > 0.02
+    srv = Server(dtype="c64", mem_budget=1 << 20, slots_per_n=4, make_batch=FakeBatch, clock=FakeClock())
+    done = srv.run(reqs)
+    assert len(done) == 40
+    for r in done:
+        assert r.error is None
+        assert r.admitted >= r.arrival
+        assert r.done >= r.admitted
+        assert r.latency >= 0.0
+    st = srv.stats()
+    assert st["seconds"] >= window
+    assert st["circuits_per_s"] <= 40 / window
+
+
+def test_largest_qubit_count_after_smaller_groups_is_not_starved():
+    """Groups are sized at first use; a later, larger qubit count that no
+    longer fits takes the memory of idle groups instead of waiting forever."""
+    FakeBatch.log = []
+    # n=8 slot: 4 KiB; n=10 slot: 16 KiB; budget 64 KiB
+    srv = Server(dtype="c64", mem_budget=64 * 1024, slots_per_n=16, make_batch=FakeBatch, clock=FakeClock())
+    small = [Request(rid=i, n=n, theta=np.full((2, 2, n), 0.01 * i)) for i, n in enumerate((8, 9, 8, 9, 8, 9))]
+    done = srv.run(small, timeout=5.0)
+    assert len(done) == 6
+    assert srv.used_bytes() > 64 * 1024 - 16 * 1024     # the small groups hold the budget
+    big = Request(rid=100, n=10, theta=np.full((3, 2, 10), 0.5))
+    done = srv.run([big], timeout=5.0)
+    assert done == [big]
+    assert big.error is None and big.result == pytest.approx(_expected(big))
+    assert any(e[0] == "create" and e[1] == 10 for e in FakeBatch.log)
