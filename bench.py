@@ -15,6 +15,8 @@ Sections on the same line (one GPU, rank 0):
   per_gate_n30  the headline circuit through the per-gate kernels
   random_n30    a random circuit with the 13-gate mix of the n = 10
                 workload, at n = 30 (general fused engines)
+  capacity_n34  Grover and the layered circuit at n = 34 complex128
+                (256 GiB, in place: no room for a second buffer)
   dax_sweep     materialised DAX / DAS MTP and MVM of m identical gates
   rh_methods    the paper's four RH sign methods for H^(x)n, n = 12..16
   qnn           serving 4096 requests (continuous batching vs one circuit
@@ -49,7 +51,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "amplitude-updates/s"
 FALLBACK_HBM_GBS = 6800.0
-ALL_SECTIONS = ("grover", "per_gate", "random", "dax", "rh", "qnn")
+ALL_SECTIONS = ("grover", "per_gate", "random", "capacity", "dax", "rh", "qnn")
 
 
 def _args(argv=None):
@@ -479,6 +481,22 @@ def _section_random(peak, peak_kind):
     return _section_statevector("random", 30, "fused", 3, 3, peak, peak_kind, check)
 
 
+def _section_capacity(peak, peak_kind):
+    """n = 34 complex128 (2^34 amplitudes, 256 GiB): the largest state the
+    GPU holds; every pass runs in place."""
+    import torch
+    from paper_2411_15332_gb300 import inputs
+    n = 34
+    free, total = torch.cuda.mem_get_info()
+    if free < (16 << n) + (4 << 30):
+        return {"skipped": f"{free >> 30} GiB free, {(16 << n) >> 30} GiB needed"}
+    m = inputs.grover_marked(n, seed=3)
+    out = {"grover_n34": _section_statevector("grover", n, "fused", 1, 1, peak, peak_kind,
+                                              lambda t, ops: _grover_error(t, n, m)),
+           "layered_n34": _section_statevector("layered", n, "fused", 1, 1, peak, peak_kind, _layered_check(n))}
+    return out
+
+
 def _section_dax(peak):
     """m identical gates filling n qubits (the paper's MTP / MVM sweeps):
     the layer operator built by m - 1 device Kronecker products (MTP), then
@@ -805,10 +823,12 @@ def run_mera(args, rank, world, local_rank):
         fns = {"grover": lambda: _section_grover(peak, peak_kind),
                "per_gate": lambda: _section_per_gate(peak, peak_kind),
                "random": lambda: _section_random(peak, peak_kind),
+               "capacity": lambda: _section_capacity(peak, peak_kind),
                "dax": lambda: _section_dax(peak),
                "rh": lambda: _section_rh(peak),
                "qnn": lambda: _section_qnn(args)}
-        keys = {"grover": "grover_n33", "per_gate": "per_gate_n30", "random": "random_n30", "dax": "dax_sweep",
+        keys = {"grover": "grover_n33", "per_gate": "per_gate_n30", "random": "random_n30",
+                "capacity": "capacity_n34", "dax": "dax_sweep",
                 "rh": "rh_methods", "qnn": "qnn"}
         for s in todo:
             try:

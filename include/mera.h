@@ -168,8 +168,8 @@ int mera_apply_circuit(mera_state* s, const mera_op* ops, size_t nops, int mode)
 
 /* Describe how MERA_MODE_FUSED would run ops[0..nops-1] on n qubits of
  * `dtype`, without touching a GPU: a header line (tile bits, passes,
- * whether the complex128 state stays int64 fixed point across passes and
- * whether its roundings are dithered), then one line per tile pass (tile
+ * whether the complex128 state stays int64 fixed point across passes),
+ * then one line per tile pass (tile
  * bits, arithmetic engine, Hadamard levels, register phases, op kinds,
  * the kernel that runs it: "stream" / "pipelined" (Hadamard-pass kernel) /
  * neither (general tile kernel), permutation runs on its loads / stores

@@ -172,7 +172,7 @@ def gate_matrix(name: str, params=()) -> np.ndarray:
 
 def plan_summary(n: int, ops, dtype: str = "c128") -> str:
     """How the fused mode would run ``ops`` (host only, no GPU needed): a
-    header line (tile bits, passes, resident / dither flags), then one line
+    header line (tile bits, passes, whether the state stays fixed point), then one line
     per pass (engine, Hadamard levels, phases, op kinds, the kernel that
     runs it, gathers / scatters, resident scaling); see mera_plan_summary."""
     arr, keep = L.ops_to_array(ops)

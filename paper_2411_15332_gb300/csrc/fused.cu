@@ -469,10 +469,10 @@ struct PassBuilder {
     int add_coef(cplx c) { return add_coef(c, i64); }
     int add_coef(cplx c, bool q62) {
         MERA_RETURN_IF(ncoef >= TILE_MAX_COEF, MERA_EUNSUPPORTED, "tile pass coefficient table full");
-        A.coef[ncoef++] = engine == ENG_Q ? enc_split(c) : enc<V>(c, q62);
+        A.coef[ncoef++] = (engine == ENG_Q || engine == ENG_I64) ? enc_split(c) : enc<V>(c, q62);
         return MERA_OK;
     }
-    // split Q61 limbs (ENG_Q coefficients and tables), |re|, |im| <= 1
+    // split Q61 limbs (int64-engine coefficients and tables), |re|, |im| <= 1
     static V enc_split(cplx d) {
         const double sc = 2305843009213693952.0;   // 2^61
         const long long r = std::llround(d.real() * sc), i = std::llround(d.imag() * sc);
@@ -485,8 +485,8 @@ struct PassBuilder {
     // complex128 separable-diagonal tables and their per-tile factors are
     // Q62 fixed point in every engine (integer multiplies)
     bool tq62() const { return sizeof(V) == 16; }
-    // a table entry: ENG_Q splits each Q61 part into 31-bit limbs
-    V enc_tab(cplx d) const { return engine == ENG_Q ? enc_split(d) : enc<V>(d, tq62()); }
+    // a table entry: the int64 engines split each Q61 part into 31-bit limbs
+    V enc_tab(cplx d) const { return (engine == ENG_Q || engine == ENG_I64) ? enc_split(d) : enc<V>(d, tq62()); }
 
     // A run of diagonal gates (they commute): single-qubit factors become one
     // separable diagonal (or exact Z4 terms when all are unit phases), unit-
@@ -695,7 +695,16 @@ struct PassBuilder {
                 for (int s2 = 0; s2 < 2; ++s2) o->codes |= (uint32_t)phase_code_f(P.v[s2]) << (3 * s2);
             } else {
                 o->type = TOP_G1;
-                for (int s2 = 0; s2 < 4; ++s2) MERA_TRY(add_coef(P.m[s2]));
+                bool ri = true;
+                for (int s2 = 0; s2 < 4; ++s2) {
+                    MERA_TRY(add_coef(P.m[s2]));
+                    if (P.m[s2].imag() != 0.0) {
+                        if (P.m[s2].real() != 0.0) ri = false;
+                        else o->flags |= 1u << s2;   // imaginary entry
+                    }
+                }
+                if (ri) o->flags |= G1_RI;
+                else o->flags = 0;
             }
             return MERA_OK;
         }
@@ -782,11 +791,12 @@ struct PassBuilder {
         A.nh = nh;
         bool exact = true;
         for (int idx : p.ops) exact = exact && op_is_exact(ops[idx]);
-        // FP64 issues about one operation per clock per SM on GB300, so
-        // complex128 passes with butterflies run the int64 engine; the
-        // others stay in float64 storage, where moves and sign flips are
-        // exact and table multiplies run in integer arithmetic
-        i64 = allow_i64 && !fp_only && nh > 0;
+        // FP64 issues about two operations per clock per SM on GB300, so
+        // complex128 passes with butterflies or any multiply run the int64
+        // engine (block floating point per tile, 31-bit-limb products); a
+        // pass of moves and sign flips only stays in float64, where they are
+        // exact
+        i64 = allow_i64 && !fp_only && (nh > 0 || !exact);
         engine = i64 ? ENG_I64 : ENG_FP;
         if (qres) {
             i64 = true;
@@ -1482,6 +1492,41 @@ static bool hpass_ok(const PassArgs<V>& A, int eng, int K) {
     return true;
 }
 
+// Per-tile int64 in the Hadamard-pass kernel (butterflies and exact sign
+// terms): a rounded right shift by half the pending levels at every phase
+// exit, so that the headroom above the tile maximum covers the growth
+// between two exits instead of the whole pass.  Bounds of the growth in
+// bits: the max norm at most doubles per unscaled level and halves per
+// shifted bit; the 2-norm of the tile (at most 2^(K/2) times its maximum
+// element) grows by sqrt(2) per unscaled level and halves per shifted bit,
+// and bounds every element.  The headroom is the smaller bound plus one.
+// cin: a level left unscaled by the previous int64 pass (the stored values
+// carry a factor sqrt(2)); cout: one level to leave for the next.
+template <typename V>
+static void hpass_i64_scaling(PassArgs<V>& A, int cin, int cout) {
+    int pending = cin, grow = 0, peak = 0, l2peak = 0;
+    for (int ph = 0; ph < A.nph; ++ph) {
+        int lv = 0;
+        for (int o = A.ph[ph].op_begin; o < A.ph[ph].op_end; ++o) lv += A.ops[o].type == TOP_H;
+        pending += lv;
+        grow += lv;
+        peak = std::max(peak, grow);
+        // 2-norm growth in half bits: the levels applied here less the bits
+        // shifted away (a carried-in level is already in the tile maximum)
+        l2peak = std::max(l2peak, pending - cin);
+        A.ph[ph].qsh = 0;
+        if (ph + 1 < A.nph && pending >= 2) {
+            const int q = pending / 2;
+            A.ph[ph].qsh = (int8_t)q;
+            pending -= 2 * q;
+            grow -= q;
+        }
+    }
+    A.qend = pending - cout;
+    const int l2 = (l2peak + A.K + 1) / 2;
+    A.guard = std::min(peak, l2) + 1;
+}
+
 template <typename V>
 int fused_build(int n, const std::vector<PrepOp>& ops, FusedPlan<V>& plan, bool fp_only, bool resident_ok) {
     plan.K = fused_tile_bits(sizeof(V) == 16 ? MERA_C128 : MERA_C64, n);
@@ -1497,24 +1542,20 @@ int fused_build(int n, const std::vector<PrepOp>& ops, FusedPlan<V>& plan, bool 
     plan.hpass.assign(passes.size(), 0);
     plan.tabs.clear();
     // resident fixed point: complex128, unitary gates only (the norm bounds
-    // every amplitude), and some arithmetic to gain from it
+    // every amplitude), some arithmetic to gain from it, and every mixing
+    // (non-monomial) gate before the first monomial one.  The monomial body
+    // keeps each amplitude's magnitude, so a global scale costs it no
+    // precision and nothing later concentrates rounding errors.  Circuits
+    // with mixing gates after the body (Hadamard layers between sign flips,
+    // as in Grover) keep float64 storage: with one global scale a small
+    // amplitude keeps fewer bits, and a later Hadamard layer sums the
+    // errors of 2^(n/2) of them into one amplitude
     plan.resident = false;
     plan.qguard = 0;
-    plan.dither = false;
-    bool mixed = false;
-    // MERA_RESIDENT=0 keeps complex128 states in float64 between passes
-    // (per-tile int64 inside Hadamard passes)
+    // MERA_RESIDENT=0 keeps every complex128 state in float64 between passes
     if (const char* e = getenv("MERA_RESIDENT"))
         if (atoi(e) == 0) resident_ok = false;
     if (sizeof(V) == 16 && !fp_only && resident_ok) {
-        // unitary gates only (the norm bounds every amplitude) and some
-        // arithmetic.  Where every mixing (non-monomial) gate precedes the
-        // first monomial one, the monomial body keeps each amplitude's
-        // magnitude, so the global scale costs it no precision and nothing
-        // later concentrates rounding errors.  Otherwise (Hadamard layers
-        // between sign flips, as in Grover) only if every tile pass runs the
-        // Hadamard-pass kernel, whose dithered rounding keeps the errors of
-        // equal amplitudes uncorrelated (checked after the passes are built)
         bool unit = true, arith = false, body = false, mixed_after = false;
         for (const PrepOp& P : ops) {
             if (P.kind == KIND_IDENTITY) continue;
@@ -1527,8 +1568,7 @@ int fused_build(int n, const std::vector<PrepOp>& ops, FusedPlan<V>& plan, bool 
             if (monomial) body = true;
             else if (body) mixed_after = true;
         }
-        plan.resident = unit && arith;
-        mixed = mixed_after;
+        plan.resident = unit && arith && !mixed_after;
     }
     for (size_t i = 0; i < passes.size(); ++i) {
         if (passes[i].single >= 0) {
@@ -1579,32 +1619,25 @@ int fused_build(int n, const std::vector<PrepOp>& ops, FusedPlan<V>& plan, bool 
         plan.feat[i] = (unsigned char)round_feat(plan.eng[i], b.features(), sizeof(V) == 16);
         plan.hpass[i] = hpass_ok(plan.args[i], plan.eng[i], plan.K) ? 1 : 0;
     }
-    if (plan.resident && mixed)
+    // int64 passes on float64 storage scale their levels by 2^(-qend/2).  The
+    // scale is linear, so a pass with an odd level count leaves one level (a
+    // factor sqrt(2) on the stored state) to the next int64 pass, whatever
+    // runs in between; only the circuit's last int64 pass multiplies by
+    // 1/sqrt(2)
+    if (!plan.resident && sizeof(V) == 16) {
+        int last = -1;
         for (size_t i = 0; i < passes.size(); ++i)
-            if (plan.single[i] < 0 && !plan.hpass[i]) return fused_build(n, ops, plan, fp_only, false);
-    plan.dither = plan.resident && mixed;
-    if (plan.dither) {
-        // Every tile pass runs the Hadamard-pass kernel: one rounding per
-        // pass (no scaling at phase exits; headroom for all the pass's
-        // levels), and an odd level count leaves a factor sqrt(2) on the
-        // stored state (value * 2^(S - g) * sqrt(2)^p) for the next pass to
-        // take, so only a run's last pass may multiply by 1/sqrt(2)
-        plan.qguard = 0;
-        int pend = 0;
+            if (plan.single[i] < 0 && plan.eng[i] == ENG_I64) last = (int)i;
+        int carry = 0;
         for (size_t i = 0; i < passes.size(); ++i) {
-            if (plan.single[i] >= 0) {
-                pend = 0;
-                continue;
-            }
+            if (plan.single[i] >= 0 || plan.eng[i] != ENG_I64) continue;
             PassArgs<V>& A = plan.args[i];
-            const bool last = i + 1 == passes.size() || plan.single[i + 1] >= 0;
+            const int tot = A.nh + carry;
+            const int cout = (int)i == last ? 0 : (tot & 1);
             for (int ph = 0; ph < A.nph; ++ph) A.ph[ph].qsh = 0;
-            const int tot = A.nh + pend;
-            const int pout = last ? 0 : (tot & 1);
-            A.qend = tot - pout;
-            A.qgi = (tot + 1) / 2 + 2;
-            plan.qguard = std::max(plan.qguard, A.qgi);
-            pend = pout;
+            if (plan.hpass[i]) hpass_i64_scaling(A, carry, cout);
+            else A.qend = tot - cout;
+            carry = cout;
         }
     }
     // resident segments: runs of tile passes between per-gate ops; the first
@@ -1764,8 +1797,6 @@ int fused_launch(const FusedPlan<V>& plan, size_t i, PassArgs<V>& A, unsigned ny
                 g >>= 1;
             }
         h.ntiles = (unsigned)tiles;
-        h.salt = 0x9E3779B9u * (uint32_t)(i + 1) ^ 0x7F4A7C15u;
-        h.dither = plan.dither ? 1 : 0;
         for (int ph = 0; ph < A.nph; ++ph)
             for (int r = 0; r < FR; ++r) h.gm[ph][r] = 1ull << A.tpos[A.ph[ph].rb[r]];
         // parity masks of the sign terms on the scattered store index
@@ -1805,7 +1836,7 @@ int fused_launch(const FusedPlan<V>& plan, size_t i, PassArgs<V>& A, unsigned ny
             }
         const void* fn = tile_fn_hpass(plan.eng[i], plan.eng[i] == ENG_Q && !A.q_in ? 1 : 0,
                                        plan.eng[i] == ENG_Q && A.q_out ? 1 : 0,
-                                       plan.eng[i] == ENG_Q ? (A.qend & 1) : 1);
+                                       A.qend & 1);
         const size_t hsm = ((size_t)1 << K) * sizeof(V);
         MERA_TRY(opt_in_smem(fn, hsm));
         void* args[] = {reinterpret_cast<void*>(&A), &h};
@@ -1994,8 +2025,8 @@ static int describe_fused(int n, int dtype, const std::vector<PrepOp>& ops, std:
     MERA_TRY(fused_build<V>(n, ops, plan, false, true));
     const int K = plan.K;
     char line[640];
-    snprintf(line, sizeof(line), "K=%d L=%d passes=%zu resident=%d dither=%d qguard=%d table_bytes=%zu\n", K,
-             low_bits_for(dtype, K), plan.args.size(), plan.resident ? 1 : 0, plan.dither ? 1 : 0, plan.qguard,
+    snprintf(line, sizeof(line), "K=%d L=%d passes=%zu resident=%d qguard=%d table_bytes=%zu\n", K,
+             low_bits_for(dtype, K), plan.args.size(), plan.resident ? 1 : 0, plan.qguard,
              plan.tabs.size() * sizeof(V));
     *out += line;
     static const char* eng_name[3] = {"fp", "i64", "q"};
@@ -2019,8 +2050,8 @@ static int describe_fused(int n, int dtype, const std::vector<PrepOp>& ops, std:
             if (A.ops[o].type == TOP_Z4) nterms += A.ops[o].aux2;
         dsep += " z4_terms=" + std::to_string(nterms) + (plan.dpass[i] ? " stream" : "") +
                 (plan.hpass[i] ? " pipelined" : "") + (A.gather ? " gather" : "") + (A.scatter ? " scatter" : "");
-        if (plan.eng[i] == ENG_Q) {
-            // resident scaling: levels scaled at phase exits (2 * shift) and at the end
+        if (plan.eng[i] == ENG_Q || (plan.eng[i] == ENG_I64 && plan.hpass[i])) {
+            // int64 scaling: levels scaled at phase exits (2 * shift) and at the end
             int exits = 0;
             for (int ph = 0; ph < A.nph; ++ph) exits += 2 * A.ph[ph].qsh;
             dsep += " qend=" + std::to_string(A.qend) + " qexit=" + std::to_string(exits) + " qgi=" +

@@ -115,16 +115,20 @@ static V mk(double re, double im) {
     return r;
 }
 
-// A coefficient for the tile passes: plain values, or Q62 fixed point
-// (value * 2^62 as int64 in the same 16 bytes) for the int64 engine.
+// A coefficient for the tile passes: plain values, or for the int64 engine
+// each part as round(value * 2^61) split into 31-bit limbs h * 2^31 + l
+// (int32 h, l for the real part, then for the imaginary part; the same 16
+// bytes).
 template <typename V>
-static V mkq(double re, double im, bool q62) {
-    if (!q62 || sizeof(V) != 16) return mk<V>(re, im);
-    const double sc = 4611686018427387904.0;   // 2^62
-    const long long q[2] = {std::llround(re * sc), std::llround(im * sc)};
-    V r;
-    memcpy(&r, q, sizeof(r));
-    return r;
+static V mkq(double re, double im, bool q61) {
+    if (!q61 || sizeof(V) != 16) return mk<V>(re, im);
+    const double sc = 2305843009213693952.0;   // 2^61
+    const long long r = std::llround(re * sc), i = std::llround(im * sc);
+    const int32_t w[4] = {(int32_t)(r >> 31), (int32_t)(r & 0x7FFFFFFF), (int32_t)(i >> 31),
+                          (int32_t)(i & 0x7FFFFFFF)};
+    V v;
+    memcpy(&v, w, sizeof(v));
+    return v;
 }
 
 // ---------------------------------------------------------------- kernels --
@@ -343,7 +347,7 @@ static int batch_layer_t(mera_batch* b, const int* slots, int nslots, const doub
         MERA_RETURN_IF(!plan->tabs.empty(), MERA_EUNSUPPORTED, "unexpected diagonal tables in the layer plan");
         b->layer_plan = plan;
     }
-    const bool q62 = !plan->eng.empty() && plan->eng[0] == 1;
+    const bool q61 = !plan->eng.empty() && plan->eng[0] == 1;
     // per-row coefficients: RZ(b) RY(a) for every qubit
     std::vector<V> cf((size_t)nslots * n * 4);
     for (int r = 0; r < nslots; ++r)
@@ -353,10 +357,10 @@ static int batch_layer_t(mera_batch* b, const int* slots, int nslots, const doub
             const double c = std::cos(a / 2), s = std::sin(a / 2);
             const double er = std::cos(bb / 2), ei = std::sin(bb / 2);   // e^{ib/2}
             V* m = &cf[((size_t)r * n + q) * 4];
-            m[0] = mkq<V>(er * c, -ei * c, q62);      // e^{-ib/2} c
-            m[1] = mkq<V>(-er * s, ei * s, q62);      // -e^{-ib/2} s
-            m[2] = mkq<V>(er * s, ei * s, q62);       // e^{ib/2} s
-            m[3] = mkq<V>(er * c, ei * c, q62);       // e^{ib/2} c
+            m[0] = mkq<V>(er * c, -ei * c, q61);      // e^{-ib/2} c
+            m[1] = mkq<V>(-er * s, ei * s, q61);      // -e^{-ib/2} s
+            m[2] = mkq<V>(er * s, ei * s, q61);       // e^{ib/2} s
+            m[3] = mkq<V>(er * c, ei * c, q61);       // e^{ib/2} c
         }
     MERA_TRY(grow(&b->coef, &b->coef_bytes, cf.size() * sizeof(V)));
     MERA_CHECK_CUDA(cudaMemcpyAsync(b->coef, cf.data(), cf.size() * sizeof(V), cudaMemcpyHostToDevice, b->stream));

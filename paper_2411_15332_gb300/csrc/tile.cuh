@@ -28,12 +28,14 @@
 //              planner uses it for circuits whose mixing gates all precede
 //              a monomial body (phases and permutations keep every
 //              amplitude's magnitude, so a global scale loses nothing).
-//  * ENG_I64 : complex128 states.  The tile is converted once to int64
-//              block floating point (one exponent per tile): butterflies are
-//              exact integer adds, permutations and {1, i, -1, -i} phases are
-//              moves and sign flips, and every multiplication is a Q62
-//              fixed-point product (full 128-bit product, ~13 integer ops);
-//              the pass's 2^{-m/2} Hadamard scale is applied on the way out.
+//  * ENG_I64 : complex128 states kept as float64 in HBM.  The tile is
+//              converted once to int64 block floating point (one exponent
+//              per tile, from the tile maximum): butterflies are exact
+//              integer adds, permutations and {1, i, -1, -i} phases are moves
+//              and sign flips, and every multiplication is the same rounded
+//              product of 31-bit limbs as in ENG_Q; the pass's 2^{-m/2}
+//              Hadamard scale is applied at phase exits (in the Hadamard-
+//              pass kernel) and on the way out.
 // In both engines a run of diagonal gates folds into exact sign / i terms
 // (TOP_Z4) and one table lookup plus one complex multiply per amplitude
 // (TOP_DSEP).
@@ -73,6 +75,10 @@ enum TileOpType : int8_t {
     TOP_Z4 = 9,       // product of exact phases i^e over pattern terms
 };
 
+// TOP_G1 flags: bit s (s = 0..3) set when matrix entry s is imaginary;
+// G1_RI when every entry is real or imaginary
+constexpr uint32_t G1_RI = 16u;
+
 struct TileOp {
     int8_t type;
     int8_t a, b, c;      // register bits (a is the most significant sub-index bit); c: 1 = per-state
@@ -80,7 +86,7 @@ struct TileOp {
     int8_t nt;           // diag: number of targets; dsep: non-tile factors
     int8_t tq[3];        // diag: global target positions (tq[0] most significant)
     int32_t coef;        // first coefficient in PassArgs::coef
-    uint32_t flags;      // diag: bit s set when sub-index s changes
+    uint32_t flags;      // diag: bit s set when sub-index s changes; g1: see G1_RI
     uint32_t codes;      // phase codes, 3 bits per row / sub-index
     uint32_t perm;       // monomial: source sub-index of row s, 3 bits per row
     int32_t aux;         // dsep: table offset (elements); z4: first term
@@ -133,7 +139,7 @@ struct TilePhase {
     int8_t rb[FR];       // local tile bits held in registers, ascending
     int16_t op_begin, op_end;
     int8_t permuted;     // 1: the exit map differs from the entry map (all reads finish first)
-    int8_t qsh;          // ENG_Q: rounded right shift at the exit (part of the 2^(-nh/2) scale)
+    int8_t qsh;          // int64 engines: rounded right shift at the exit (part of the 2^(-nh/2) scale)
     XSide in;            // slots this phase reads (from the previous exchange or the load staging)
     XOut out;            // slots this phase writes (next exchange or the store staging)
 };
@@ -158,7 +164,8 @@ struct PassArgs {
     int nh;              // Hadamard butterflies in the pass (ENG_I64 / ENG_Q scale by 2^-nh/2)
     int q_in, q_out;     // ENG_Q: 1 = the state is read / written as fixed point, 0 = as doubles
     int qgi, qgo;        // ENG_Q: headroom bits of the input / output format (value * 2^(*qS - g))
-    int qend;            // ENG_Q: Hadamard levels still unscaled at the end of the pass
+    int qend;            // int64 engines: Hadamard levels scaled at the end of the pass (the rest
+                         // went at phase exits, qsh; ENG_I64 may carry one level to another pass)
     const int* qS;       // ENG_Q: device address of S = 59 - floor(log2 of a norm bound)
     int guard;           // ENG_I64: headroom bits of the fixed-point format
     int tpos[16];        // global bit of local bit j, ascending
@@ -424,6 +431,20 @@ __device__ __forceinline__ I2 qcmul(int4 d, I2 x) {
     r.y = k1 + k2;
     return r;
 }
+// d * x for a coefficient d that is real (imag == 0: limbs d.x, d.y of its
+// real part) or imaginary (limbs d.z, d.w of its imaginary part): two real
+// products instead of the three of a general complex product
+__device__ __forceinline__ I2 qrimul(int4 d, uint32_t imag, I2 x) {
+    I2 r;
+    if (!imag) {
+        r.x = qmul_q(x.x, d.x, d.y);
+        r.y = qmul_q(x.y, d.x, d.y);
+    } else {
+        r.x = -qmul_q(x.y, d.z, d.w);
+        r.y = qmul_q(x.x, d.z, d.w);
+    }
+    return r;
+}
 // x * c for a real Q61 constant c = ch * 2^31 + cl
 __device__ __forceinline__ long long qmul_real(long long x, int ch, int cl) {
     int h, l;
@@ -442,8 +463,22 @@ template <typename V, int B, int ENG>
 __device__ __forceinline__ void op_g1(V (&x)[FRA], const TileOp& o, const V* cf, uint64_t gb, const uint64_t* gm) {
     const uint32_t act = active16(o.cmask, o.cvals, gb, gm);
     if (act == 0) return;
-    if constexpr (ENG == ENG_Q) {
+    if constexpr (ENG == ENG_Q || ENG == ENG_I64) {
         const int4 q0 = qcoef(cf, 0), q1 = qcoef(cf, 1), q2 = qcoef(cf, 2), q3 = qcoef(cf, 3);
+        if (o.flags & G1_RI) {
+            // every entry real or imaginary (RX, RY, ...): two real products each
+            const uint32_t im = o.flags;
+#pragma unroll
+            for (int j = 0; j < FRA; ++j) {
+                if (j & (1 << B)) continue;
+                const int j1 = j | (1 << B);
+                if (!(act & (1u << j))) continue;
+                const V a0 = x[j], a1 = x[j1];
+                x[j] = vadd(qrimul(q0, im & 1u, a0), qrimul(q1, im & 2u, a1));
+                x[j1] = vadd(qrimul(q2, im & 4u, a0), qrimul(q3, im & 8u, a1));
+            }
+            return;
+        }
 #pragma unroll
         for (int j = 0; j < FRA; ++j) {
             if (j & (1 << B)) continue;
@@ -543,7 +578,7 @@ __device__ __forceinline__ void op_g2(V (&x)[FRA], const TileOp& o, const V* cf,
                     if (src == u) v = in[u];
                 x[id[s]] = mul_ik(v, code_at(o.codes, s) & 3);
             }
-        } else if constexpr (ENG == ENG_Q) {
+        } else if constexpr (ENG == ENG_Q || ENG == ENG_I64) {
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 V acc = qcmul(qcoef(cf, r * 4), in[0]);
@@ -575,7 +610,7 @@ __device__ __forceinline__ void op_diag(V (&x)[FRA], const TileOp& o, const V* c
         for (int t = 0; t < o.nt; ++t) sub = (sub << 1) | (int)((g >> o.tq[t]) & 1ull);
         if (!((o.flags >> sub) & 1u)) continue;
         const int code = code_at(o.codes, sub);
-        if constexpr (ENG == ENG_Q) {
+        if constexpr (ENG == ENG_Q || ENG == ENG_I64) {
             x[j] = code < 4 ? mul_ik(x[j], code) : qcmul(qcoef(cf, sub), x[j]);
         } else {
             x[j] = phase_any(code, cf[sub], x[j]);
@@ -616,8 +651,8 @@ __device__ __forceinline__ void op_dsep(V (&x)[FRA], const TileOp& o, const V* c
     const int nsel = o.nt < DSEP_SEL_BITS ? o.nt : DSEP_SEL_BITS;
     uint32_t sel = 0;
     for (int f = 0; f < nsel; ++f) sel |= (uint32_t)((gb >> ntq[o.aux2 + f]) & 1ull) << f;
-    if constexpr (ENG == ENG_Q) {
-        // split-Q61 tables; per-tile factors (Q62) multiply separately
+    if constexpr (ENG == ENG_Q || ENG == ENG_I64) {
+        // split-Q61 tables; per-tile factors multiply separately
         const int4* t = reinterpret_cast<const int4*>(tab) + o.aux + ((size_t)sel << K);
         // groups of four entries in flight (an empty asm with a memory
         // clobber keeps the compiler from hoisting all sixteen loads)
@@ -941,16 +976,17 @@ __global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
                 }
             }
         } else if constexpr (ENG == ENG_I64) {
-            // undo the fixed-point scale and apply 2^(-nh/2)
-            const int So = S + (a.nh >> 1);
-            const bool odd = a.nh & 1;
-            const long long r2 = 3260954456333195553ll;   // round(2^62 / sqrt(2))
+            // undo the fixed-point scale and apply 2^(-qend/2) (the pass's
+            // levels, with a level carried in from or left to another pass)
+            const int So = S + (a.qend >> 1);
+            const bool odd = a.qend & 1;
+            const int r2h = 759250124, r2l = 2134625280;   // round(2^61 / sqrt(2)) = r2h * 2^31 + r2l
 #pragma unroll
             for (int j = 0; j < FRA; ++j) {
                 long long vx = x[j].x, vy = x[j].y;
                 if (odd) {
-                    vx = __mul64hi(vx, r2) << 2;
-                    vy = __mul64hi(vy, r2) << 2;
+                    vx = qmul_real(vx, r2h, r2l);
+                    vy = qmul_real(vy, r2h, r2l);
                 }
                 x[j].x = __double_as_longlong(fix2d(vx, So));
                 x[j].y = __double_as_longlong(fix2d(vy, So));
@@ -998,7 +1034,7 @@ __global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
 
 // --------------------------------------------------- Hadamard passes --
 // Passes of butterflies and exact sign terms only (the Hadamard layers of
-// Sec. III-C's RH path), int64 engines, one state.  Persistent: two CTAs
+// Sec. III-B's RH path), int64 engines, one state.  Persistent: two CTAs
 // per SM walk the tiles blockIdx.x, blockIdx.x + gridDim.x, ...; each
 // reads its tiles through one shared-memory buffer, and as soon as the last
 // phase of a tile has read the buffer the next tile's asynchronous copy
@@ -1015,8 +1051,6 @@ struct HPassArgs {
     unsigned long long ntmask;     // non-tile global bits (below n)
     unsigned long long dstride;    // gridDim.x deposited into the non-tile bits
     unsigned ntiles;
-    unsigned salt;                 // ENG_Q: per-pass seed of the rounding dither
-    int dither;                    // ENG_Q: 1 = dithered rounding, 0 = to nearest (ties up)
     unsigned long long gm[HP_MAXPH][FR];   // per phase: global bit of each register bit
     // per op: a run of butterflies on distinct register bits starting here
     // (bits 0..3: the bits, bits 4..7: the run's length in ops), else 0
@@ -1026,55 +1060,6 @@ struct HPassArgs {
     // scatter map; the first two pattern bits' P in the low / high halves
     unsigned pz[TILE_MAX_Z4];
 };
-
-// Dithered rounding (ENG_Q in this kernel).  After a Hadamard layer the
-// amplitudes of a state are often equal in magnitude; rounded the same way
-// they carry equal errors, which the next Hadamard layer adds up coherently
-// (2^(n/2) of them into one amplitude).  Each rounding of this kernel
-// therefore adds a pseudo-random increment u in [0, 2^k) before a k-bit
-// right shift: floor((v + u) / 2^k) is unbiased, and the errors of equal
-// amplitudes become uncorrelated.  u comes from a nonlinear hash (the
-// 32-bit finaliser of MurmurHash3) of the amplitude's global index, the
-// pass and the rounding site, so results do not depend on the launch shape
-// (a hash linear over GF(2) would correlate with the Walsh functions the
-// next layer projects on).  Circuits without a mixing gate after their
-// monomial body need no dither (nothing later concentrates the errors):
-// there d = 0x80008000 makes u = 2^(k-1), rounding to nearest.
-__device__ __forceinline__ uint32_t hp_hash(uint64_t g, uint32_t salt) {
-    uint32_t h = (uint32_t)g ^ ((uint32_t)(g >> 32) * 0x9E3779B9u) ^ salt;
-    h ^= h >> 16;
-    h *= 0x85EBCA6Bu;
-    h ^= h >> 13;
-    h *= 0xC2B2AE35u;
-    h ^= h >> 16;
-    return h;
-}
-// 16 random bits d scaled to [0, 2^k), 1 <= k <= 63
-__device__ __forceinline__ long long hp_dk(uint32_t d16, int k) {
-    return (long long)(((unsigned long long)d16 << 48) >> (64 - k));
-}
-// x * c / 2^61 (Q61 constant c = ch * 2^31 + cl) with the final 30-bit
-// rounding dithered
-__device__ __forceinline__ long long hp_qmul_real(long long x, int ch, int cl, uint32_t d16) {
-    int h, l;
-    qsplit(x, h, l);
-    const long long m1 = (long long)h * ch;
-    const long long m2 = (long long)h * cl + (long long)l * ch + qlow(l, cl);
-    return 2 * m1 + ((m2 + ((long long)d16 << 14)) >> 30);
-}
-// d2fix with the rounding of dropped bits dithered
-__device__ __forceinline__ long long hp_d2fix(double v, int S, uint32_t d16) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-    const int e = (int)((b >> 52) & 0x7FF);
-    if (e == 0) return 0;
-    const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    const int sh = S + e - 1075;
-    unsigned long long a;
-    if (sh >= 0) a = m << sh;
-    else if (sh > -64) a = (m + (unsigned long long)hp_dk(d16, -sh)) >> (-sh);
-    else a = 0;
-    return (b >> 63) ? -(long long)a : (long long)a;
-}
 
 __device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
@@ -1094,23 +1079,6 @@ __device__ __forceinline__ long long shr_lt32(long long v, int k) {
     const int nhi = (int)hi >> k;
     return (long long)(((unsigned long long)(unsigned)nhi << 32) | nlo);
 }
-// 16 dither bits d scaled to [0, 2^k), 1 <= k < 32
-__device__ __forceinline__ long long dk_lt32(unsigned d16, int k) {
-    return (long long)(k <= 16 ? (d16 >> (16 - k)) : (d16 << (k - 16)));
-}
-// Dither of register slot j from the thread's hash t (a bijective multiply
-// of t ^ j's constant): re and im take two 16-bit fields.  Without dither
-// both are 0x8000 (round to nearest, ties up).
-__device__ __forceinline__ void hp_dj(uint32_t t, int j, bool dither, unsigned& re, unsigned& im) {
-    if (!dither) {
-        re = im = 0x8000u;
-        return;
-    }
-    const uint32_t d = (t ^ (0x9E3779B9u * (uint32_t)(j + 1))) * 0x2C1B3C6Du;
-    re = d >> 16;
-    im = (d >> 4) & 0xFFFFu;
-}
-
 // Butterflies on the register bits set in m: a full phase (all four bits)
 // as one straight block, otherwise bit by bit.
 template <typename V>
@@ -1129,8 +1097,8 @@ __device__ __forceinline__ void op_hmask(V (&x)[FRA], int m) {
 }
 
 // QOUT (ENG_Q): 1 = the pass writes the fixed-point format, 0 = doubles
-// (the last pass of a run); ODD (ENG_Q): 0 = the pass's level count to
-// scale away is even (no 1/sqrt(2) product).  Separate instantiations keep
+// (the last pass of a run); ODD: 0 = the pass's level count to scale away
+// is even (no 1/sqrt(2) product).  Separate instantiations keep
 // code a pass never runs out of its instruction stream.
 template <int ENG, int QIN, int QOUT, int ODD>
 __global__ void __launch_bounds__(HP_THREADS, HP_CTAS_PER_SM)
@@ -1195,7 +1163,6 @@ __global__ void __launch_bounds__(HP_THREADS, HP_CTAS_PER_SM)
     uint64_t tb = insert_zeros(blockIdx.x, a.tpos, K);   // base of the tile being worked on
     __syncthreads();
     prefetch(blockIdx.x, tb);
-    const bool dither = ENG == ENG_Q && h.dither;
     for (uint64_t tile = blockIdx.x; tile < h.ntiles; tile += G) {
         cp_async_wait<0>();
         __syncthreads();   // this tile is in the buffer
@@ -1217,13 +1184,10 @@ __global__ void __launch_bounds__(HP_THREADS, HP_CTAS_PER_SM)
 #pragma unroll
                 for (int j = 0; j < FRA; ++j) x[j] = raw_load<double2, V>(sms[sb ^ dep4x(j, sr)]);
                 if constexpr (ENG == ENG_Q && QIN == 1) {
-                    const uint32_t t = dither ? hp_hash(gb, h.salt) : 0u;
 #pragma unroll
                     for (int j = 0; j < FRA; ++j) {
-                        unsigned dr, di;
-                        hp_dj(t, j, dither, dr, di);
-                        x[j].x = hp_d2fix(__longlong_as_double(x[j].x), S, dr);
-                        x[j].y = hp_d2fix(__longlong_as_double(x[j].y), S, di);
+                        x[j].x = d2fix(__longlong_as_double(x[j].x), S);
+                        x[j].y = d2fix(__longlong_as_double(x[j].y), S);
                     }
                 }
                 if constexpr (ENG == ENG_I64) {
@@ -1313,17 +1277,15 @@ __global__ void __launch_bounds__(HP_THREADS, HP_CTAS_PER_SM)
             for (int i = 0; i < ph.out.noff; ++i)
                 if ((gb >> ph.out.offq[i]) & 1ull) ob ^= (int)ph.out.offv[i];
             if (p != a.nph - 1) {
-                if constexpr (ENG == ENG_Q) {
-                    if (ph.qsh > 0) {
-                        const int k = ph.qsh;
-                        const uint32_t t = dither ? hp_hash(gb, h.salt ^ (0x51ED27u * (uint32_t)(p + 1))) : 0u;
+                // part of the 2^(-nh/2) scale at the phase exit: a right
+                // shift rounded to nearest (ties up), both engines
+                if (ph.qsh > 0) {
+                    const int k = ph.qsh;
+                    const long long half = 1ll << (k - 1);
 #pragma unroll
-                        for (int j = 0; j < FRA; ++j) {
-                            unsigned dr, di;
-                            hp_dj(t, j, dither, dr, di);
-                            x[j].x = shr_lt32(x[j].x + dk_lt32(dr, k), k);
-                            x[j].y = shr_lt32(x[j].y + dk_lt32(di, k), k);
-                        }
+                    for (int j = 0; j < FRA; ++j) {
+                        x[j].x = shr_lt32(x[j].x + half, k);
+                        x[j].y = shr_lt32(x[j].y + half, k);
                     }
                 }
 #pragma unroll
@@ -1334,27 +1296,24 @@ __global__ void __launch_bounds__(HP_THREADS, HP_CTAS_PER_SM)
             double2* out = reinterpret_cast<double2*>(x);
             if constexpr (ENG == ENG_Q) {
                 // the pass's 2^(-qend/2) and the change to the next pass's
-                // format: one dithered (or nearest) shift, times 1/sqrt(2)
+                // format: one shift rounded to nearest, times 1/sqrt(2)
                 // for odd qend; then doubles unless the state stays fixed point
                 const int k = (a.qend >> 1) + (a.q_out ? a.qgo - a.qgi : 0);
                 const bool odd = ODD && (a.qend & 1);
                 const int r2h = 759250124, r2l = 2134625280;   // round(2^61 / sqrt(2)) = r2h * 2^31 + r2l
-                const uint32_t t = dither ? hp_hash(gb, h.salt) : 0u;
+                const long long half = k > 0 ? (1ll << (k - 1)) : 0ll;
 #pragma unroll
                 for (int j = 0; j < FRA; ++j) {
                     long long vx = x[j].x, vy = x[j].y;
-                    unsigned dr, di;
-                    hp_dj(t, j, dither, dr, di);
                     if constexpr (ODD == 1) {
                         if (odd) {
-                            vx = hp_qmul_real(vx, r2h, r2l, dr);
-                            vy = hp_qmul_real(vy, r2h, r2l, di);
-                            hp_dj(t ^ 0x5BD1E995u, j, dither, dr, di);
+                            vx = qmul_real(vx, r2h, r2l);
+                            vy = qmul_real(vy, r2h, r2l);
                         }
                     }
                     if (k > 0) {
-                        vx = shr_lt32(vx + dk_lt32(dr, k), k);
-                        vy = shr_lt32(vy + dk_lt32(di, k), k);
+                        vx = shr_lt32(vx + half, k);
+                        vy = shr_lt32(vy + half, k);
                     } else if (k < 0) {
                         vx = (long long)((unsigned long long)vx << (-k));
                         vy = (long long)((unsigned long long)vy << (-k));
@@ -1368,15 +1327,16 @@ __global__ void __launch_bounds__(HP_THREADS, HP_CTAS_PER_SM)
                     }
                 }
             } else {
-                const int So = S + (a.nh >> 1);
-                const bool odd = a.nh & 1;
-                const long long r2 = 3260954456333195553ll;   // round(2^62 / sqrt(2))
+                // levels left unscaled by the phase exits: 2^(-qend/2)
+                const int So = S + (a.qend >> 1);
+                const bool odd = ODD && (a.qend & 1);
+                const int r2h = 759250124, r2l = 2134625280;   // round(2^61 / sqrt(2)) = r2h * 2^31 + r2l
 #pragma unroll
                 for (int j = 0; j < FRA; ++j) {
                     long long vx = x[j].x, vy = x[j].y;
                     if (odd) {
-                        vx = __mul64hi(vx, r2) << 2;
-                        vy = __mul64hi(vy, r2) << 2;
+                        vx = qmul_real(vx, r2h, r2l);
+                        vy = qmul_real(vy, r2h, r2l);
                     }
                     x[j].x = __double_as_longlong(fix2d(vx, So));
                     x[j].y = __double_as_longlong(fix2d(vy, So));

@@ -29,7 +29,7 @@ def test_small_states(n):
     """n < 12: one tile of 2^(n-4) threads (fewer than a warp for n < 9)."""
     ops, m = inputs.grover_circuit(n, 3, seed=3)
     head, tile = _pipelined(n, ops)
-    assert "dither=1" in head and all("pipelined" in l for l in tile)
+    assert "resident=0" in head and all("pipelined" in l and "eng=i64" in l for l in tile)
     s = new_state(n)
     s.apply_circuit(ops, mode="fused")
     got = s.to_numpy()

@@ -139,11 +139,10 @@ def _grover_split(n):
 
 
 @pytest.mark.parametrize("n", [14, 17])
-def test_dithered_runs_split_by_per_gate_ops(n):
-    """Resident with dithered rounding (mixing gates after sign flips): a
-    per-gate op ends the first run, whose last pass must take the sqrt(2) an
-    odd level count left pending before writing doubles; the second run
-    starts afresh."""
+def test_hadamard_runs_split_by_per_gate_ops(n):
+    """Mixing gates after sign flips keep float64 storage; the Hadamard
+    passes (per-tile int64, scaling at phase exits, an odd level count
+    ending in a rounded 1/sqrt(2) product) on both sides of a per-gate op."""
     first, perm8, second = _grover_split(n)
     s = new_state(n)
     s.apply_circuit(first + [(perm8, (n - 1, 3, 6), (), (), 0)] + second, mode="fused")
@@ -155,9 +154,9 @@ def test_dithered_runs_split_by_per_gate_ops(n):
     assert max_err(got, ref) <= 1e-13
 
 
-def test_dithered_conversion_of_a_general_state():
-    """The first pass of a dithered run converts arbitrary doubles (not a
-    basis state) into the fixed-point format."""
+def test_hadamard_passes_on_a_general_state():
+    """Per-tile int64 Hadamard passes on arbitrary doubles (not a basis
+    state): block exponents from every tile's own maximum."""
     n = 16
     rng = np.random.default_rng(44)
     psi = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
@@ -171,9 +170,9 @@ def test_dithered_conversion_of_a_general_state():
     assert max_err(got, ref) <= 1e-13
 
 
-def test_dithered_rounding_is_reproducible():
-    """The dither comes from a hash of the amplitude index, the pass and the
-    rounding site: the same circuit gives bitwise the same state."""
+def test_hadamard_passes_are_deterministic():
+    """Rounding depends only on the values and the plan: the same circuit
+    gives bitwise the same state."""
     n = 20
     ops, _ = inputs.grover_circuit(n, 3, seed=3)
     outs = []

@@ -36,7 +36,7 @@ def parse(summary):
 
 def test_layered_n30_plan(core):
     head, passes = parse(core.plan_summary(30, inputs.layered_circuit(30, 20, seed=2)))
-    assert head["resident"] == 1 and head["passes"] == 60 and head["dither"] == 0
+    assert head["resident"] == 1 and head["passes"] == 60
     assert all(p["eng"] == "q" for p in passes)
     # the CNOT ladders ride on the exchanges: no register permutation op
     assert all(p["mono"] == "0" for p in passes)
@@ -79,16 +79,17 @@ def test_complex64_plans_use_the_float_engine(core):
     assert all(p["eng"] == "fp" for p in passes)
 
 
-def test_mixing_gates_after_the_body_need_the_dithered_kernel(core):
-    """Grover: Hadamard layers after phase flips.  With one global scale,
-    equal amplitudes carry equal rounding errors that a later Hadamard layer
-    would add up coherently; the state stays fixed point only because every
-    tile pass runs the Hadamard-pass kernel, whose rounding is dithered."""
+def test_mixing_gates_after_the_body_keep_doubles(core):
+    """Grover: Hadamard layers after phase flips.  With one global scale a
+    small amplitude keeps fewer bits and a later Hadamard layer adds up the
+    errors of many amplitudes, so the state keeps float64 storage; every
+    tile pass runs the Hadamard-pass kernel in its per-tile int64 engine
+    (exponent from the tile maximum), loads staged through shared memory."""
     ops, _ = inputs.grover_circuit(24, 4, seed=3)
     summary = core.plan_summary(24, ops)
     head, passes = parse(summary)
-    assert head["resident"] == 1 and head["dither"] == 1
-    assert all(p["eng"] == "q" for p in passes)
+    assert head["resident"] == 0
+    assert all(p["eng"] == "i64" for p in passes)
     lines = summary.splitlines()[1:]
     assert all("pipelined" in l for l in lines)
     assert all(p["load_smem"] == "1" for p in passes)
@@ -108,9 +109,9 @@ def test_mixing_gates_after_the_body_without_the_kernel_keep_doubles(core):
     assert head["resident"] == 0
     assert all(p["eng"] in ("i64", "fp") for p in passes if not p.get("single"))
 
-def test_dithered_plan_split_by_a_per_gate_op(core):
-    """A three-target gate between Hadamard layers and sign flips: two runs
-    of Hadamard-pass kernels, still resident with dithered rounding."""
+def test_hadamard_passes_around_a_per_gate_op(core):
+    """A three-target gate between Hadamard layers and sign flips: per-tile
+    int64 Hadamard-pass kernels on both sides of the per-gate op."""
     n = 17
     m = inputs.grover_marked(n, seed=7)
     perm8 = np.roll(np.eye(8, dtype=np.complex128), 1, axis=0)
@@ -118,37 +119,51 @@ def test_dithered_plan_split_by_a_per_gate_op(core):
            + [(perm8, (n - 1, 3, 6), (), (), 0)] + [inputs.flip_index(n, 0)] + inputs.hadamard_all(n))
     summary = core.plan_summary(n, ops)
     head, passes = parse(summary)
-    assert head["resident"] == 1 and head["dither"] == 1
+    assert head["resident"] == 0
     assert sum(1 for p in passes if p.get("single")) == 1
     tile = [l for l in summary.splitlines()[1:] if "per-gate" not in l]
-    assert tile and all("pipelined" in l for l in tile)
+    assert tile and all("pipelined" in l and "eng=i64" in l for l in tile)
+
+
+def _phase_levels(p):
+    return [int(x.rstrip("p")) for x in p["phase_ops"].split(",")]
 
 
 @pytest.mark.parametrize("n,iters", [(33, 8), (20, 3), (13, 2)])
-def test_dithered_scaling_takes_every_level_once(core, n, iters):
-    """Resident scaling in a dithered plan: no scaling at phase exits; a
-    pass inside a run scales an even number of levels (an odd count leaves
-    sqrt(2) for the next pass); the run's last pass takes what is left, so
-    over the circuit every butterfly level is scaled exactly once."""
+def test_int64_hadamard_passes_scale_at_phase_exits(core, n, iters):
+    """Per-tile int64 Hadamard passes take part of the 2^(-nh/2) scale at
+    every phase exit (a shift by half the pending levels): every level of
+    the circuit is scaled once, and the headroom over the tile
+    maximum is the smaller of the max-norm and 2-norm growth bounds between
+    two exits, plus one bit -- at most 9 bits for a K = 12 tile, where a
+    whole 12-level pass unscaled would need 13."""
     ops, _ = inputs.grover_circuit(n, iters, seed=3)
     head, passes = parse(core.plan_summary(n, ops))
-    assert head["dither"] == 1
-    assert all(int(p["qexit"]) == 0 for p in passes)
-    assert all(int(p["qend"]) % 2 == 0 for p in passes[:-1])
-    assert sum(int(p["qend"]) for p in passes) == sum(int(p["nh"]) for p in passes) == n * (2 * iters + 1)
-    # headroom: every level pending at once, the carried factor included
-    pend = 0
-    for p in passes:
-        tot = int(p["nh"]) + pend
-        assert int(p["qgi"]) == (tot + 1) // 2 + 2
-        pend = tot - int(p["qend"])
+    K = head["K"]
+    assert head["resident"] == 0
+    carry = 0
+    for k, p in enumerate(passes):
+        nh, qexit, qend = int(p["nh"]), int(p["qexit"]), int(p["qend"])
+        # an odd level count leaves one level (sqrt(2) on the stored state)
+        # to the next pass; only the last pass may scale an odd count
+        cout = nh + carry - qexit - qend
+        assert cout in (0, 1) and (k + 1 < len(passes) or cout == 0)
+        assert qend % 2 == 0 or k + 1 == len(passes)
+        carry = cout
+        levels = _phase_levels(p)       # sign-term ops are in the counts too, butterflies dominate
+        if len(levels) > 1 and nh >= 4:
+            assert qexit > 0
+        assert int(p["guard"]) <= min(nh, (nh + K + 1) // 2) + 1
+        if K == 12 and nh >= 9:
+            assert int(p["guard"]) <= 9
+    assert sum(int(p["qexit"]) + int(p["qend"]) for p in passes) == n * (2 * iters + 1)
 
 
-def test_resident_scaling_without_dither_uses_exits(core):
-    """Without dither (the layered circuit) a pass scales at phase exits once
-    8 levels are pending and the rest at its end; every level once."""
+def test_resident_scaling_uses_exits(core):
+    """The layered circuit (resident) scales at phase exits once 8 levels are
+    pending and the rest at its end; every level once."""
     head, passes = parse(core.plan_summary(30, inputs.layered_circuit(30, 20, seed=2)))
-    assert head["dither"] == 0
+    assert head["resident"] == 1
     assert sum(int(p["qend"]) + int(p["qexit"]) for p in passes) == sum(int(p["nh"]) for p in passes) == 30
     assert any(int(p["qexit"]) > 0 for p in passes)
 
