@@ -1640,6 +1640,30 @@ int fused_build(int n, const std::vector<PrepOp>& ops, FusedPlan<V>& plan, bool 
             carry = cout;
         }
     }
+    // A run of consecutive Hadamard passes in the per-tile int64 engine of a
+    // unitary circuit keeps the state between them in the per-amplitude
+    // exponent format (no conversion to doubles and back; its bias comes
+    // from the norm bound, which unitary passes keep): the run's first pass
+    // reads doubles, its last writes doubles
+    plan.efmt = false;
+    if (!plan.resident && sizeof(V) == 16 && !fp_only && resident_ok) {
+        bool unit = true;
+        for (const PrepOp& P : ops) {
+            if (P.kind == KIND_IDENTITY) continue;
+            double rs;
+            bool u;
+            op_gain(P, &rs, &u);
+            unit = unit && u && P.bslot < 0;
+        }
+        auto hp = [&](size_t k) { return plan.single[k] < 0 && plan.eng[k] == ENG_I64 && plan.hpass[k]; };
+        for (size_t i = 0; unit && i < passes.size(); ++i) {
+            if (!hp(i)) continue;
+            PassArgs<V>& A = plan.args[i];
+            A.q_in = (i > 0 && hp(i - 1)) ? 1 : 0;
+            A.q_out = (i + 1 < passes.size() && hp(i + 1)) ? 1 : 0;
+            if (A.q_in || A.q_out) plan.efmt = true;
+        }
+    }
     // resident segments: runs of tile passes between per-gate ops; the first
     // reads doubles, the last writes doubles
     plan.dpass.assign(passes.size(), 0);
@@ -1834,9 +1858,7 @@ int fused_launch(const FusedPlan<V>& plan, size_t i, PassArgs<V>& A, unsigned ny
                 h.hrun[o] = (unsigned char)(m | (len << 4));
                 o += len;
             }
-        const void* fn = tile_fn_hpass(plan.eng[i], plan.eng[i] == ENG_Q && !A.q_in ? 1 : 0,
-                                       plan.eng[i] == ENG_Q && A.q_out ? 1 : 0,
-                                       A.qend & 1);
+        const void* fn = tile_fn_hpass(plan.eng[i], A.q_in ? 0 : 1, A.q_out ? 1 : 0, A.qend & 1);
         const size_t hsm = ((size_t)1 << K) * sizeof(V);
         MERA_TRY(opt_in_smem(fn, hsm));
         void* args[] = {reinterpret_cast<void*>(&A), &h};
@@ -1898,7 +1920,7 @@ static int upload_plan(mera_state* s, FusedPlan<V>& plan) {
 
 template <typename V>
 static int launch_plan(mera_state* s, FusedPlan<V>& plan, const std::vector<PrepOp>& ops) {
-    if (plan.resident) {
+    if (plan.resident || plan.efmt) {
         MERA_TRY(state_ensure_scratch(s, 16384));
         MERA_TRY(qscale_launch(s->data, s->n, s->scratch, s->stream));
         const int* qS = reinterpret_cast<const int*>(reinterpret_cast<char*>(s->scratch) + 8192);
@@ -2025,8 +2047,8 @@ static int describe_fused(int n, int dtype, const std::vector<PrepOp>& ops, std:
     MERA_TRY(fused_build<V>(n, ops, plan, false, true));
     const int K = plan.K;
     char line[640];
-    snprintf(line, sizeof(line), "K=%d L=%d passes=%zu resident=%d qguard=%d table_bytes=%zu\n", K,
-             low_bits_for(dtype, K), plan.args.size(), plan.resident ? 1 : 0, plan.qguard,
+    snprintf(line, sizeof(line), "K=%d L=%d passes=%zu resident=%d efmt=%d qguard=%d table_bytes=%zu\n", K,
+             low_bits_for(dtype, K), plan.args.size(), plan.resident ? 1 : 0, plan.efmt ? 1 : 0, plan.qguard,
              plan.tabs.size() * sizeof(V));
     *out += line;
     static const char* eng_name[3] = {"fp", "i64", "q"};

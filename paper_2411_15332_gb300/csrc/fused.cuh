@@ -21,6 +21,7 @@ struct FusedPlan {
     std::vector<unsigned char> hpass;     // 1: Hadamard / sign-term pass for the pipelined kernel
     bool resident = false;                // complex128 state kept as int64 fixed point (ENG_Q)
     int qguard = 0;                       // ENG_Q: headroom bits above the state norm
+    bool efmt = false;                    // ENG_I64 Hadamard runs keep per-amplitude exponents between passes
 };
 
 // fp_only: every pass in the float engine (coefficients as plain values).

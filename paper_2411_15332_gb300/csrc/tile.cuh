@@ -1079,6 +1079,37 @@ __device__ __forceinline__ long long shr_lt32(long long v, int k) {
     const int nhi = (int)hi >> k;
     return (long long)(((unsigned long long)(unsigned)nhi << 32) | nlo);
 }
+// Per-amplitude exponent format of the int64 engine between Hadamard passes
+// (EF).  A complex128 amplitude is two int64 words: bits 6..63 of each hold
+// a signed mantissa (re, im), bits 0..5 of the real word the amplitude's
+// exponent code e (0..63), bits 0..5 of the imaginary word are 0; value =
+// mantissa * 2^-(e + B), B a bias fixed per circuit from the state's norm
+// bound.  A stored amplitude has max(|re|, |im|) in [2^55, 2^56] (56
+// significant bits, more than a double's 53) unless it is below the
+// normal range, where e = 63 keeps it unnormalised (zero included).
+constexpr int EF_LZ = 8;          // leading zeros of a normalised mantissa word before the shift by 6
+
+// round(v / 2^s), s >= 1 (0 for s >= 63)
+__device__ __forceinline__ long long ef_rshift(long long v, int s) {
+    if (s >= 63) return 0;
+    return (v + (1ll << (s - 1))) >> s;
+}
+// amplitude (vx, vy) = value * 2^T into the two EF words
+__device__ __forceinline__ double2 ef_store(long long vx, long long vy, int T, int B) {
+    const unsigned long long a = (unsigned long long)((vx < 0 ? -vx : vx) | (vy < 0 ? -vy : vy));
+    if (a == 0) return make_double2(__longlong_as_double(63ll), 0.0);
+    int sl = __clzll((long long)a) - EF_LZ;     // shift that puts the top bit at 55
+    int e = T + sl - B;
+    if (e > 63) {                               // below the normal range
+        sl -= e - 63;
+        e = 63;
+    }
+    const long long mx = sl >= 0 ? (long long)((unsigned long long)vx << sl) : ef_rshift(vx, -sl);
+    const long long my = sl >= 0 ? (long long)((unsigned long long)vy << sl) : ef_rshift(vy, -sl);
+    return make_double2(__longlong_as_double((long long)(((unsigned long long)mx << 6) | (unsigned)e)),
+                        __longlong_as_double((long long)((unsigned long long)my << 6)));
+}
+
 // Butterflies on the register bits set in m: a full phase (all four bits)
 // as one straight block, otherwise bit by bit.
 template <typename V>
@@ -1096,9 +1127,10 @@ __device__ __forceinline__ void op_hmask(V (&x)[FRA], int m) {
     if (m & 8) op_h<V, 3>(x);
 }
 
-// QOUT (ENG_Q): 1 = the pass writes the fixed-point format, 0 = doubles
-// (the last pass of a run); ODD: 0 = the pass's level count to scale away
-// is even (no 1/sqrt(2) product).  Separate instantiations keep
+// QIN: 1 = the pass converts its input from doubles, 0 = it reads the
+// engine's format (ENG_Q: global fixed point; ENG_I64: EF); QOUT: 1 = the
+// pass writes that format, 0 = doubles (the last pass of a run); ODD: 0 =
+// the pass's level count to scale away is even (no 1/sqrt(2) product).  Separate instantiations keep
 // code a pass never runs out of its instruction stream.
 template <int ENG, int QIN, int QOUT, int ODD>
 __global__ void __launch_bounds__(HP_THREADS, HP_CTAS_PER_SM)
@@ -1114,8 +1146,10 @@ __global__ void __launch_bounds__(HP_THREADS, HP_CTAS_PER_SM)
     const uint32_t tid = threadIdx.x;
     double2* const psi = a.psi;
     double2* const pso = a.psi_out ? a.psi_out : a.psi;   // tiles are disjoint: out of place is free
-    int Sq = 0;
+    int Sq = 0, B = 0;
     if constexpr (ENG == ENG_Q) Sq = *a.qS - a.qgi;
+    // EF bias: amplitudes are below 2^(60 - *qS); code 0 holds up to 16x that
+    if constexpr (ENG == ENG_I64 && (QIN == 0 || QOUT == 1)) B = *a.qS - 8;
     // per phase and thread (tile-independent): global offset of register
     // slot 0, and the entry / exit slot bases in shared memory
     for (int p = 0; p < a.nph; ++p) {
@@ -1190,7 +1224,7 @@ __global__ void __launch_bounds__(HP_THREADS, HP_CTAS_PER_SM)
                         x[j].y = d2fix(__longlong_as_double(x[j].y), S);
                     }
                 }
-                if constexpr (ENG == ENG_I64) {
+                if constexpr (ENG == ENG_I64 && QIN == 1) {
                     int e = 0;
 #pragma unroll
                     for (int j = 0; j < FRA; ++j)
@@ -1206,6 +1240,35 @@ __global__ void __launch_bounds__(HP_THREADS, HP_CTAS_PER_SM)
                     for (int j = 0; j < FRA; ++j) {
                         x[j].x = d2fix(__longlong_as_double(x[j].x), S);
                         x[j].y = d2fix(__longlong_as_double(x[j].y), S);
+                    }
+                } else if constexpr (ENG == ENG_I64) {
+                    // EF input: the tile takes the scale of its largest
+                    // amplitude (smallest code, zeros hold 63) with the
+                    // pass's headroom; each mantissa is aligned to it by a
+                    // rounded shift
+                    int e = 63;
+#pragma unroll
+                    for (int j = 0; j < FRA; ++j) e = min(e, (int)(x[j].x & 63));
+                    const unsigned amask = T >= 32 ? 0xffffffffu : ((1u << T) - 1u);
+                    e = (int)__reduce_min_sync(amask, (unsigned)e);
+                    if ((tid & 31) == 0) s_emax[tid >> 5] = e;
+                    __syncthreads();
+                    int emin = 63;
+                    for (int w = 0; w < (int)((T + 31) >> 5); ++w) emin = min(emin, s_emax[w]);
+                    // |mantissa| <= 2^56 at code emin becomes < 2^(62 - guard)
+                    const int sh0 = a.guard - 6 - emin;
+                    S = emin + B + 6 - a.guard;
+#pragma unroll
+                    for (int j = 0; j < FRA; ++j) {
+                        const int sh = (int)(x[j].x & 63) + sh0;
+                        const long long mx = x[j].x >> 6, my = x[j].y >> 6;
+                        if (sh > 0) {
+                            x[j].x = ef_rshift(mx, sh);
+                            x[j].y = ef_rshift(my, sh);
+                        } else {
+                            x[j].x = (long long)((unsigned long long)mx << (-sh));
+                            x[j].y = (long long)((unsigned long long)my << (-sh));
+                        }
                     }
                 }
             } else {
@@ -1327,7 +1390,8 @@ __global__ void __launch_bounds__(HP_THREADS, HP_CTAS_PER_SM)
                     }
                 }
             } else {
-                // levels left unscaled by the phase exits: 2^(-qend/2)
+                // levels left unscaled by the phase exits: 2^(-qend/2), a
+                // change of scale (doubles) or of exponent code (EF)
                 const int So = S + (a.qend >> 1);
                 const bool odd = ODD && (a.qend & 1);
                 const int r2h = 759250124, r2l = 2134625280;   // round(2^61 / sqrt(2)) = r2h * 2^31 + r2l
@@ -1338,8 +1402,14 @@ __global__ void __launch_bounds__(HP_THREADS, HP_CTAS_PER_SM)
                         vx = qmul_real(vx, r2h, r2l);
                         vy = qmul_real(vy, r2h, r2l);
                     }
-                    x[j].x = __double_as_longlong(fix2d(vx, So));
-                    x[j].y = __double_as_longlong(fix2d(vy, So));
+                    if constexpr (QOUT == 1) {
+                        const double2 w = ef_store(vx, vy, So, B);
+                        x[j].x = __double_as_longlong(w.x);
+                        x[j].y = __double_as_longlong(w.y);
+                    } else {
+                        x[j].x = __double_as_longlong(fix2d(vx, So));
+                        x[j].y = __double_as_longlong(fix2d(vy, So));
+                    }
                 }
             }
             if (ENG == ENG_Q && a.scatter) {

@@ -13,8 +13,9 @@ const void* tile_fn_q(int feat, int qin);
 // the streaming kernel of single-phase table passes (resident engine)
 const void* tile_fn_dpass();
 const void* tile_fn_i64(int feat, int qin);
-// the Hadamard-pass kernel (ENG_I64 or ENG_Q): qin / qout = 1 when the pass
-// reads / writes doubles resp. fixed point (ENG_Q), odd = 1 when its level
+// the Hadamard-pass kernel (ENG_I64 or ENG_Q): qin = 1 when the pass reads
+// doubles, qout = 1 when it writes the engine's own format (ENG_Q: global
+// fixed point; ENG_I64: per-amplitude exponents), odd = 1 when its level
 // count to scale away may be odd
 const void* tile_fn_hpass(int eng, int qin, int qout, int odd);
 const void* tile_fn_fp(int feat, int qin);

@@ -14,6 +14,11 @@ const void* tile_fn_hpass(int eng, int qin, int qout, int odd) {
         if (qin) return qout ? hpass_q<1, 1>(odd) : hpass_q<1, 0>(odd);
         return qout ? hpass_q<0, 1>(odd) : hpass_q<0, 0>(odd);
     }
+    if (qin) {
+        if (qout) return odd ? (const void*)k_hpass<ENG_I64, 1, 1, 1> : (const void*)k_hpass<ENG_I64, 1, 1, 0>;
+        return odd ? (const void*)k_hpass<ENG_I64, 1, 0, 1> : (const void*)k_hpass<ENG_I64, 1, 0, 0>;
+    }
+    if (qout) return odd ? (const void*)k_hpass<ENG_I64, 0, 1, 1> : (const void*)k_hpass<ENG_I64, 0, 1, 0>;
     return odd ? (const void*)k_hpass<ENG_I64, 0, 0, 1> : (const void*)k_hpass<ENG_I64, 0, 0, 0>;
 }
 

@@ -95,6 +95,26 @@ def test_mixing_gates_after_the_body_keep_doubles(core):
     assert all(p["load_smem"] == "1" for p in passes)
 
 
+def test_hadamard_runs_keep_per_amplitude_exponents(core):
+    """Consecutive int64 Hadamard passes of a unitary circuit pass the state
+    on in the per-amplitude exponent format: only the run's first pass reads
+    doubles and only its last writes doubles."""
+    ops, _ = inputs.grover_circuit(24, 4, seed=3)
+    head, passes = parse(core.plan_summary(24, ops))
+    assert head["efmt"] == 1
+    assert passes[0]["q_in"] == "0" and passes[-1]["q_out"] == "0"
+    assert all(p["q_in"] == "1" for p in passes[1:]) and all(p["q_out"] == "1" for p in passes[:-1])
+
+
+def test_non_unitary_circuit_keeps_doubles_between_hadamard_passes(core):
+    n = 14
+    m = np.diag([2.0, 0.5]).astype(np.complex128)
+    ops = inputs.hadamard_all(n) + [inputs.flip_index(n, 5)] + inputs.hadamard_all(n) + [(m, (3,), (), (), 0)]
+    head, passes = parse(core.plan_summary(n, ops))
+    assert head["efmt"] == 0 and head["resident"] == 0
+    assert all(p.get("q_in", "0") == "0" and p.get("q_out", "0") == "0" for p in passes if not p.get("single"))
+
+
 def test_mixing_gates_after_the_body_without_the_kernel_keep_doubles(core):
     """A table pass (RZ on every qubit) between Hadamard layers does not run
     the Hadamard-pass kernel, so that circuit keeps double storage (per-tile
