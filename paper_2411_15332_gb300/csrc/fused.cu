@@ -1389,8 +1389,8 @@ int launch_tile<float2>(int, int, dim3 grid, unsigned block, size_t smem, cudaSt
 // Build every pass of a circuit: kernel arguments (without state pointers),
 // engine and kernel variant per pass, and the diagonal tables.  Passes with
 // `single` >= 0 are per-gate ops (returned in `singles`, -1 otherwise).
-// Arguments of the streaming kernel from a single-phase pass (K = 12,
-// n <= 32): per thread-index bit and register bit the global index masks
+// Arguments of the streaming kernel from a single-phase pass (K = 12):
+// per thread-index bit and register bit the global index masks
 // of the load, the store and the natural positions, and the local masks.
 // Thread bits 0..7 are the phase's non-register bits, thread bit 8 its top
 // register bit; register bits 0..2 its lower register bits.
@@ -1428,7 +1428,7 @@ static void dpass_args(const PassArgs<V>& A, int n, DPassArgs& d) {
         ++d.nruns;
         i += w;
     }
-    auto g32 = [&](int local) { return (uint32_t)1u << A.tpos[local]; };
+    auto g32 = [&](int local) { return 1ull << A.tpos[local]; };
     for (int t = 0; t < 8; ++t) {
         d.nat.t[t] = g32(nr[t]);
         d.tloc[t] = 1u << nr[t];
@@ -1440,14 +1440,14 @@ static void dpass_args(const PassArgs<V>& A, int n, DPassArgs& d) {
         d.rloc[r] = 1u << ph.rb[r];
     }
     auto from_g = [&](const GMap& g, DMap& m) {
-        for (int t = 0; t < 8; ++t) m.t[t] = (uint32_t)g.tc[t];
-        m.t[8] = (uint32_t)g.rc[3];
-        for (int r = 0; r < 3; ++r) m.r[r] = (uint32_t)g.rc[r];
-        m.c = (uint32_t)g.c;
+        for (int t = 0; t < 8; ++t) m.t[t] = g.tc[t];
+        m.t[8] = g.rc[3];
+        for (int r = 0; r < 3; ++r) m.r[r] = g.rc[r];
+        m.c = g.c;
         m.nq = g.nq;
         for (int i = 0; i < g.nq; ++i) {
             m.q[i] = g.q[i];
-            m.w[i] = (uint32_t)g.w[i];
+            m.w[i] = g.w[i];
         }
     };
     d.in = d.nat;
@@ -1465,8 +1465,8 @@ static void dpass_args(const PassArgs<V>& A, int n, DPassArgs& d) {
         } else if (op.type == TOP_Z4) {
             for (int z = 0; z < op.aux2; ++z) {
                 const Z4Term& t = A.z4[op.aux + z];
-                d.z4[d.nz].mask = (uint32_t)t.mask;
-                d.z4[d.nz].vals = (uint32_t)t.vals;
+                d.z4[d.nz].mask = t.mask;
+                d.z4[d.nz].vals = t.vals;
                 d.z4[d.nz].e = t.e;
                 d.z4[d.nz].post = op.c == 2 ? 1 : 0;
                 ++d.nz;
@@ -1677,9 +1677,8 @@ int fused_build(int n, const std::vector<PrepOp>& ops, FusedPlan<V>& plan, bool 
             A.q_out = (i + 1 < np && plan.single[i + 1] < 0) ? 1 : 0;
             A.qgo = A.q_out ? plan.args[i + 1].qgi : A.qgi;
             // single phase of tables and sign terms between fixed-point
-            // passes of a state of at most 2^32 amplitudes: the streaming kernel
-            bool ok = A.nph == 1 && A.q_in && A.q_out && A.qend == 0 && !A.load_smem && !A.store_smem && n <= 32 &&
-                      plan.K == 12;
+            // passes: the streaming kernel
+            bool ok = A.nph == 1 && A.q_in && A.q_out && A.qend == 0 && !A.load_smem && !A.store_smem && plan.K == 12;
             int ntab = 0, nz = 0;
             for (int o = A.ph[0].op_begin; ok && o < A.ph[0].op_end; ++o) {
                 const TileOp& op = A.ops[o];
@@ -1801,7 +1800,8 @@ int fused_launch(const FusedPlan<V>& plan, size_t i, PassArgs<V>& A, unsigned ny
         const uint64_t ctas = std::max<uint64_t>(1, std::min<uint64_t>(tiles, 16ull * (uint64_t)sms));
         void* args[] = {&d};
         launch_begin(st, MERA_KCLASS_DPASS, pass_bytes);
-        MERA_CHECK_CUDA(cudaLaunchKernel(tile_fn_dpass(), dim3((unsigned)ctas, 1), dim3(2u << (K - FR)), args, 0, st));
+        MERA_CHECK_CUDA(cudaLaunchKernel(tile_fn_dpass(plan.n > 32 ? 1 : 0), dim3((unsigned)ctas, 1), dim3(2u << (K - FR)),
+                                         args, 0, st));
         return launch_end(st);
     }
     if (sizeof(V) == 16 && ny == 1 && plan.hpass[i]) {

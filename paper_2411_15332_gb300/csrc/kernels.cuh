@@ -82,6 +82,66 @@ __device__ __forceinline__ I2 cfma(I2 c, I2 a, I2 acc) {
     acc.y += mulq62(c.x, a.y) + mulq62(c.y, a.x);
     return acc;
 }
+// v * 2^-S rounded to nearest even (values below the normal range flush to 0).
+__device__ __forceinline__ double fix2d(long long v, int S) {
+    if (v == 0) return 0.0;
+    const unsigned long long sgn = v < 0 ? (1ull << 63) : 0ull;
+    const unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+    int lz = __clzll((long long)a);
+    const unsigned long long m = a << lz;
+    unsigned long long r = m >> 11;
+    const unsigned long long rem = m & 0x7FFull;
+    if (rem > 0x400ull || (rem == 0x400ull && (r & 1ull))) {
+        r += 1;
+        if (r >> 53) {
+            r >>= 1;
+            lz -= 1;
+        }
+    }
+    const int e = (63 - lz) - S + 1023;
+    if (e <= 0) return __longlong_as_double((long long)sgn);
+    return __longlong_as_double((long long)(sgn | ((unsigned long long)e << 52) | (r & 0xFFFFFFFFFFFFFull)));
+}
+
+
+// Resident fixed point: a table entry d (|d| <= 1) in Q61, each part split
+// as h * 2^31 + l with 0 <= l < 2^31 (stored as int32 rh, rl, ih, il).
+// For |x| < 2^59 split the same way, x * d / 2^61 is
+// 2 xh dh + (xh dl + xl dh + xl dl / 2^31) / 2^30: six 32x32->64
+// multiply-adds and two 32-bit high products per component, rounded to
+// nearest (error <= 1/2 unit plus 2^-30; zero stays zero, so amplitudes
+// that must vanish do not feed later butterflies).
+__device__ __forceinline__ void qsplit(long long x, int& h, int& l) {
+    h = (int)(x >> 31);
+    l = (int)((unsigned)x & 0x7FFFFFFFu);
+}
+// (a * b) >> 31 for 0 <= a, b < 2^31, to within one unit
+__device__ __forceinline__ long long qlow(int a, int b) { return (long long)(__umulhi((unsigned)a, (unsigned)b) << 1); }
+__device__ __forceinline__ long long qcombine(long long m1, long long m2) {
+    return 2 * m1 + ((m2 + (1ll << 29)) >> 30);
+}
+// x * c / 2^61 for |x| < 2^60 and a Q61 value c with |c| < 2^61.5, both
+// split into 31-bit limbs, rounded to nearest
+__device__ __forceinline__ long long qmul_q(long long x, int ch, int cl) {
+    int h, l;
+    qsplit(x, h, l);
+    return qcombine((long long)h * ch, (long long)h * cl + (long long)l * ch + qlow(l, cl));
+}
+// Complex product with three real products (c + id)(a + ib):
+// k1 = c (a + b), k2 = a (d - c), k3 = b (c + d); re = k1 - k3, im = k1 + k2
+// (each k rounded to nearest: error <= 1 unit per part, unbiased, 0 stays 0).
+__device__ __forceinline__ I2 qcmul(int4 d, I2 x) {
+    const long long c = ((long long)d.x << 31) + (long long)(unsigned)d.y;
+    const long long e = ((long long)d.z << 31) + (long long)(unsigned)d.w;
+    const long long dmc = e - c, cpd = c + e;
+    const long long k1 = qmul_q(x.x + x.y, d.x, d.y);
+    const long long k2 = qmul_q(x.x, (int)(dmc >> 31), (int)((unsigned)dmc & 0x7FFFFFFFu));
+    const long long k3 = qmul_q(x.y, (int)(cpd >> 31), (int)((unsigned)cpd & 0x7FFFFFFFu));
+    I2 r;
+    r.x = k1 - k3;
+    r.y = k1 + k2;
+    return r;
+}
 __device__ __forceinline__ long long sneg(long long v) { return -v; }
 __device__ __forceinline__ I2 neg_v(I2 x) {
     x.x = -x.x;
@@ -165,27 +225,59 @@ struct GateArgs {
     V m[64];                     // dense matrix, row-major
 };
 
-// Multiply one sub-space (controls = cbits) by a scalar.
+// Multiply one sub-space (controls = cbits) by a scalar; four amplitudes a
+// grid stride apart per thread and iteration, loads first.
 template <typename V>
 __global__ void __launch_bounds__(256) k_phase(const __grid_constant__ GateArgs<V> a) {
+    constexpr int U = 4;
     const V v = a.v[0];
     const int code = a.code[0];
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.count; t += stride) {
-        const uint64_t i = insert_zeros(t, a.ins, a.nins) | a.cbits;
-        a.psi[i] = apply_phase(code, v, a.psi[i]);
+    for (uint64_t t0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t0 < a.count; t0 += stride * U) {
+        uint64_t idx[U];
+        V x[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) idx[u] = insert_zeros(t0 + (uint64_t)u * stride, a.ins, a.nins) | a.cbits;
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (t0 + (uint64_t)u * stride < a.count) x[u] = __ldcs(a.psi + idx[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (t0 + (uint64_t)u * stride < a.count) __stcs(a.psi + idx[u], apply_phase(code, v, x[u]));
     }
 }
 
-// Diagonal gate: amplitude i (controls holding) times v[sub(i)] where v != 1.
+// Diagonal gate: amplitude i (controls holding) times v[sub(i)] where v != 1;
+// four amplitudes a grid stride apart per thread and iteration, loads
+// first.  For complex128 with general phases the complex multiply (four
+// FP64 operations) bounds it on GB300, ~2 SM clocks per amplitude against
+// an HBM budget of ~1.5; an integer product of 31-bit limbs on a share of
+// the warps was measured slower (its wide multiplies compete for the same
+// issue budget).
 template <typename V>
 __global__ void __launch_bounds__(256) k_diag(const __grid_constant__ GateArgs<V> a) {
+    constexpr int U = 4;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.count; t += stride) {
-        const uint64_t i = insert_zeros(t, a.ins, a.nins) | a.cbits;
-        int sub = 0;
-        for (int j = 0; j < a.nt; ++j) sub = (sub << 1) | (int)((i >> a.tq[j]) & 1ull);
-        if (a.flag[sub]) a.psi[i] = apply_phase(a.code[sub], a.v[sub], a.psi[i]);
+    for (uint64_t t0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t0 < a.count; t0 += stride * U) {
+        uint64_t idx[U];
+        int sub[U];
+        bool on[U];
+        V x[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint64_t t = t0 + (uint64_t)u * stride;
+            idx[u] = insert_zeros(t, a.ins, a.nins) | a.cbits;
+            int sb = 0;
+            for (int j = 0; j < a.nt; ++j) sb = (sb << 1) | (int)((idx[u] >> a.tq[j]) & 1ull);
+            sub[u] = sb;
+            on[u] = t < a.count && a.flag[sb];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (on[u]) x[u] = a.psi[idx[u]];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (on[u]) a.psi[idx[u]] = apply_phase(a.code[sub[u]], a.v[sub[u]], x[u]);
     }
 }
 

@@ -348,28 +348,6 @@ __device__ __forceinline__ long long d2fix(double v, int S) {
     return (b >> 63) ? -(long long)a : (long long)a;
 }
 
-// v * 2^-S rounded to nearest even (values below the normal range flush to 0).
-__device__ __forceinline__ double fix2d(long long v, int S) {
-    if (v == 0) return 0.0;
-    const unsigned long long sgn = v < 0 ? (1ull << 63) : 0ull;
-    const unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
-    int lz = __clzll((long long)a);
-    const unsigned long long m = a << lz;
-    unsigned long long r = m >> 11;
-    const unsigned long long rem = m & 0x7FFull;
-    if (rem > 0x400ull || (rem == 0x400ull && (r & 1ull))) {
-        r += 1;
-        if (r >> 53) {
-            r >>= 1;
-            lz -= 1;
-        }
-    }
-    const int e = (63 - lz) - S + 1023;
-    if (e <= 0) return __longlong_as_double((long long)sgn);
-    return __longlong_as_double((long long)(sgn | ((unsigned long long)e << 52) | (r & 0xFFFFFFFFFFFFFull)));
-}
-
-
 // x * d for a complex128 amplitude held as doubles and a Q62 table entry d
 // (|d| <= 1) without FP64 instructions: both parts of x are aligned to the
 // larger of their exponents as 62-bit integers, multiplied with full
@@ -393,44 +371,6 @@ __device__ __forceinline__ double2 icmul(I2 d, double2 x) {
     return make_double2(fix2d(pr, S), fix2d(pi, S));
 }
 
-// Resident fixed point: a table entry d (|d| <= 1) in Q61, each part split
-// as h * 2^31 + l with 0 <= l < 2^31 (stored as int32 rh, rl, ih, il).
-// For |x| < 2^59 split the same way, x * d / 2^61 is
-// 2 xh dh + (xh dl + xl dh + xl dl / 2^31) / 2^30: six 32x32->64
-// multiply-adds and two 32-bit high products per component, rounded to
-// nearest (error <= 1/2 unit plus 2^-30; zero stays zero, so amplitudes
-// that must vanish do not feed later butterflies).
-__device__ __forceinline__ void qsplit(long long x, int& h, int& l) {
-    h = (int)(x >> 31);
-    l = (int)((unsigned)x & 0x7FFFFFFFu);
-}
-// (a * b) >> 31 for 0 <= a, b < 2^31, to within one unit
-__device__ __forceinline__ long long qlow(int a, int b) { return (long long)(__umulhi((unsigned)a, (unsigned)b) << 1); }
-__device__ __forceinline__ long long qcombine(long long m1, long long m2) {
-    return 2 * m1 + ((m2 + (1ll << 29)) >> 30);
-}
-// x * c / 2^61 for |x| < 2^60 and a Q61 value c with |c| < 2^61.5, both
-// split into 31-bit limbs, rounded to nearest
-__device__ __forceinline__ long long qmul_q(long long x, int ch, int cl) {
-    int h, l;
-    qsplit(x, h, l);
-    return qcombine((long long)h * ch, (long long)h * cl + (long long)l * ch + qlow(l, cl));
-}
-// Complex product with three real products (c + id)(a + ib):
-// k1 = c (a + b), k2 = a (d - c), k3 = b (c + d); re = k1 - k3, im = k1 + k2
-// (each k rounded to nearest: error <= 1 unit per part, unbiased, 0 stays 0).
-__device__ __forceinline__ I2 qcmul(int4 d, I2 x) {
-    const long long c = ((long long)d.x << 31) + (long long)(unsigned)d.y;
-    const long long e = ((long long)d.z << 31) + (long long)(unsigned)d.w;
-    const long long dmc = e - c, cpd = c + e;
-    const long long k1 = qmul_q(x.x + x.y, d.x, d.y);
-    const long long k2 = qmul_q(x.x, (int)(dmc >> 31), (int)((unsigned)dmc & 0x7FFFFFFFu));
-    const long long k3 = qmul_q(x.y, (int)(cpd >> 31), (int)((unsigned)cpd & 0x7FFFFFFFu));
-    I2 r;
-    r.x = k1 - k3;
-    r.y = k1 + k2;
-    return r;
-}
 // d * x for a coefficient d that is real (imag == 0: limbs d.x, d.y of its
 // real part) or imaginary (limbs d.z, d.w of its imaginary part): two real
 // products instead of the three of a general complex product
@@ -1445,26 +1385,26 @@ __global__ void __launch_bounds__(HP_THREADS, HP_CTAS_PER_SM)
 // ------------------------------------------------ single-phase tables --
 // A resident-engine pass whose only work is one phase of diagonal tables and
 // sign terms (its permutations ride on the gathered loads and scattered
-// stores) on a state of at most 2^32 amplitudes.  512 threads per tile,
-// eight amplitudes each; every address is an XOR of masks the host
-// precomputes per thread-index bit and register bit (32-bit arithmetic), so
-// a thread's setup is a few XORs and an access is one XOR and one address
-// add.  No shared memory; with a permuted load or store every load precedes
-// every store (block barrier), since amplitudes move between threads of the
-// tile in place.
+// stores).  512 threads per tile, eight amplitudes each; every address is an
+// XOR of masks the host precomputes per thread-index bit and register bit,
+// so a thread's setup is a few XORs and an access is one XOR and one address
+// add.  IX is the index type: 32-bit arithmetic for states of at most 2^32
+// amplitudes, 64-bit above.  No shared memory; with a permuted load or
+// store every load precedes every store (block barrier), since amplitudes
+// move between threads of the tile in place.
 constexpr int DPASS_MAX_TABS = 2;
 constexpr int DPASS_TBITS = 9;     // thread-index bits (512 threads)
 constexpr int DPASS_RBITS = 3;     // register bits (8 amplitudes)
 struct DMap {                      // global index = tile base ^ c ^ thread part ^ register part ^ tile terms
-    uint32_t t[DPASS_TBITS];
-    uint32_t r[DPASS_RBITS];
-    uint32_t c;
-    uint32_t w[TILE_MAX_XOFF];
+    unsigned long long t[DPASS_TBITS];
+    unsigned long long r[DPASS_RBITS];
+    unsigned long long c;
+    unsigned long long w[TILE_MAX_XOFF];
     int8_t q[TILE_MAX_XOFF];
     int8_t nq;
 };
 struct DZ4 {
-    uint32_t mask, vals;
+    unsigned long long mask, vals;
     int16_t e;
     int16_t post;                  // 1: matched on the stored (permuted) index
 };
@@ -1487,15 +1427,24 @@ struct DPassArgs {
     DZ4 z4[TILE_MAX_Z4];
 };
 
-__device__ __forceinline__ uint32_t dbase(const DMap& m, uint32_t tid, uint32_t tb) {
-    uint32_t v = tb ^ m.c;
+template <typename IX>
+__device__ __forceinline__ IX dbase(const DMap& m, uint32_t tid, IX tb) {
+    IX v = tb ^ (IX)m.c;
 #pragma unroll
-    for (int t = 0; t < DPASS_TBITS; ++t) v ^= (0u - ((tid >> t) & 1u)) & m.t[t];
+    for (int t = 0; t < DPASS_TBITS; ++t) v ^= ((IX)0 - (IX)((tid >> t) & 1u)) & (IX)m.t[t];
     for (int i = 0; i < m.nq; ++i)
-        if ((tb >> m.q[i]) & 1u) v ^= m.w[i];
+        if ((tb >> m.q[i]) & 1u) v ^= (IX)m.w[i];
     return v;
 }
-__device__ __forceinline__ uint32_t dreg(int j, const uint32_t* r) {
+template <typename IX>
+__device__ __forceinline__ IX dreg(int j, const IX* r) {
+    IX v = 0;
+    if (j & 1) v ^= r[0];
+    if (j & 2) v ^= r[1];
+    if (j & 4) v ^= r[2];
+    return v;
+}
+__device__ __forceinline__ uint32_t dreg32(int j, const uint32_t* r) {
     uint32_t v = 0;
     if (j & 1) v ^= r[0];
     if (j & 2) v ^= r[1];
@@ -1503,43 +1452,44 @@ __device__ __forceinline__ uint32_t dreg(int j, const uint32_t* r) {
     return v;
 }
 
-template <int GROUP>
+template <int GROUP, typename IX>
 __global__ void __launch_bounds__(512, 2) k_dpass(const __grid_constant__ DPassArgs a) {
     constexpr int NA = 1 << DPASS_RBITS;
     const uint32_t tid = threadIdx.x;
     // the thread's parts of the maps are the same in every tile
-    const uint32_t ti = dbase(a.in, tid, 0), to = dbase(a.out, tid, 0), tn = dbase(a.nat, tid, 0);
+    const IX ti = dbase<IX>(a.in, tid, 0), to = dbase<IX>(a.out, tid, 0), tn = dbase<IX>(a.nat, tid, 0);
     uint32_t lb = 0;
 #pragma unroll
     for (int t = 0; t < DPASS_TBITS; ++t) lb ^= (0u - ((tid >> t) & 1u)) & a.tloc[t];
-    uint32_t rin[DPASS_RBITS], rout[DPASS_RBITS], rnat[DPASS_RBITS], rloc[DPASS_RBITS];
+    IX rin[DPASS_RBITS], rout[DPASS_RBITS], rnat[DPASS_RBITS];
+    uint32_t rloc[DPASS_RBITS];
 #pragma unroll
     for (int r = 0; r < DPASS_RBITS; ++r) {
-        rin[r] = a.in.r[r];
-        rout[r] = a.out.r[r];
-        rnat[r] = a.nat.r[r];
+        rin[r] = (IX)a.in.r[r];
+        rout[r] = (IX)a.out.r[r];
+        rnat[r] = (IX)a.nat.r[r];
         rloc[r] = a.rloc[r];
     }
     // several tiles per CTA (grid-stride), each as in a one-tile launch
     for (uint32_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-    uint32_t tb = 0;
-    for (int i = 0; i < a.nruns; ++i) tb |= ((tile >> a.run_src[i]) & ((1u << a.run_w[i]) - 1u)) << a.run_dst[i];
-    uint32_t gi0 = tb ^ ti, go0 = tb ^ to;
-    const uint32_t gn0 = tb ^ tn;
+    IX tb = 0;
+    for (int i = 0; i < a.nruns; ++i) tb |= (IX)((tile >> a.run_src[i]) & ((1u << a.run_w[i]) - 1u)) << a.run_dst[i];
+    IX gi0 = tb ^ ti, go0 = tb ^ to;
+    const IX gn0 = tb ^ tn;
     for (int i = 0; i < a.in.nq; ++i)
-        if ((tb >> a.in.q[i]) & 1u) gi0 ^= a.in.w[i];
+        if ((tb >> a.in.q[i]) & 1u) gi0 ^= (IX)a.in.w[i];
     for (int i = 0; i < a.out.nq; ++i)
-        if ((tb >> a.out.q[i]) & 1u) go0 ^= a.out.w[i];
+        if ((tb >> a.out.q[i]) & 1u) go0 ^= (IX)a.out.w[i];
     const int4* tabs[DPASS_MAX_TABS];
     for (int t = 0; t < a.ntab; ++t) {
         uint32_t sel = 0;
-        for (int f = 0; f < a.tab_nt[t]; ++f) sel |= ((tb >> a.tab_q[t][f]) & 1u) << f;
+        for (int f = 0; f < a.tab_nt[t]; ++f) sel |= (uint32_t)((tb >> a.tab_q[t][f]) & 1u) << f;
         tabs[t] = a.tab + a.tab_off[t] + ((size_t)sel << a.K);
     }
     I2 x[NA];
 #pragma unroll
     for (int j = 0; j < NA; ++j) {
-        const longlong2 v = __ldcs(reinterpret_cast<const longlong2*>(a.psi + (gi0 ^ dreg(j, rin))));
+        const longlong2 v = __ldcs(reinterpret_cast<const longlong2*>(a.psi + (gi0 ^ dreg<IX>(j, rin))));
         x[j].x = v.x;
         x[j].y = v.y;
     }
@@ -1551,7 +1501,7 @@ __global__ void __launch_bounds__(512, 2) k_dpass(const __grid_constant__ DPassA
         for (int t = 0; t < a.ntab; ++t) {
             int4 d[GROUP];
 #pragma unroll
-            for (int u = 0; u < GROUP; ++u) d[u] = __ldg(tabs[t] + (lb ^ dreg(g + u, rloc)));
+            for (int u = 0; u < GROUP; ++u) d[u] = __ldg(tabs[t] + (lb ^ dreg32(g + u, rloc)));
 #pragma unroll
             for (int u = 0; u < GROUP; ++u) x[g + u] = qcmul(d[u], x[g + u]);
         }
@@ -1563,8 +1513,8 @@ __global__ void __launch_bounds__(512, 2) k_dpass(const __grid_constant__ DPassA
                 const DZ4 tz = a.z4[z];
 #pragma unroll
                 for (int u = 0; u < GROUP; ++u) {
-                    const uint32_t gi = tz.post ? (go0 ^ dreg(g + u, rout)) : (gn0 ^ dreg(g + u, rnat));
-                    if ((gi & tz.mask) == tz.vals) e[u] += tz.e;
+                    const IX gi = tz.post ? (go0 ^ dreg<IX>(g + u, rout)) : (gn0 ^ dreg<IX>(g + u, rnat));
+                    if ((gi & (IX)tz.mask) == (IX)tz.vals) e[u] += tz.e;
                 }
             }
 #pragma unroll
@@ -1580,7 +1530,7 @@ __global__ void __launch_bounds__(512, 2) k_dpass(const __grid_constant__ DPassA
                 vx = (long long)((unsigned long long)vx << (-k));
                 vy = (long long)((unsigned long long)vy << (-k));
             }
-            __stcs(reinterpret_cast<longlong2*>(a.psi_out + (go0 ^ dreg(g + u, rout))), make_longlong2(vx, vy));
+            __stcs(reinterpret_cast<longlong2*>(a.psi_out + (go0 ^ dreg<IX>(g + u, rout))), make_longlong2(vx, vy));
         }
     }
     }   // tiles (disjoint index sets: no ordering between them is needed)

@@ -10,8 +10,9 @@ namespace mera {
 // complex128 kernels by engine and feature set; qin = 1 selects the
 // fixed-point variant that converts its input from doubles
 const void* tile_fn_q(int feat, int qin);
-// the streaming kernel of single-phase table passes (resident engine)
-const void* tile_fn_dpass();
+// the streaming kernel of single-phase table passes (resident engine);
+// wide = 1: 64-bit indices (states of more than 2^32 amplitudes)
+const void* tile_fn_dpass(int wide);
 const void* tile_fn_i64(int feat, int qin);
 // the Hadamard-pass kernel (ENG_I64 or ENG_Q): qin = 1 when the pass reads
 // doubles, qout = 1 when it writes the engine's own format (ENG_Q: global

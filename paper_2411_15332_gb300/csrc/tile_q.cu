@@ -4,7 +4,9 @@
 
 namespace mera {
 
-const void* tile_fn_dpass() { return (const void*)k_dpass<4>; }
+const void* tile_fn_dpass(int wide) {
+    return wide ? (const void*)k_dpass<4, unsigned long long> : (const void*)k_dpass<4, uint32_t>;
+}
 
 const void* tile_fn_q(int feat, int qin) {
     if (qin) {

@@ -178,9 +178,8 @@ def test_invalid_ops_leave_state_unchanged():
 
 
 def test_diagonal_gates_on_both_product_paths():
-    """Per-gate complex128 diagonals: general unit phases take the FP64
-    multiply in 3 of 8 warps and the integer Q62 product in the others; a
-    diagonal with |Re| > 1 stays on the FP64 multiply everywhere."""
+    """Per-gate complex128 diagonals with general unit phases, controls and
+    several targets, and a non-unitary diagonal (|Re| > 1)."""
     n = 16
     rng = np.random.default_rng(12)
     psi = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
