@@ -1482,8 +1482,8 @@ static void dpass_args(const PassArgs<V>& A, int n, DPassArgs& d) {
 template <typename V>
 static bool hpass_ok(const PassArgs<V>& A, int eng, int K) {
     if (sizeof(V) != 16 || (eng != ENG_I64 && eng != ENG_Q)) return false;
-    if (A.gather || A.nph > HP_MAXPH || (1 << (K - FR)) > HP_THREADS) return false;
-    if (((size_t)1 << K) * sizeof(V) > 64 * 1024) return false;
+    // 256 threads for tiles of up to 2^12 amplitudes; 512 (2^13) in the per-tile engine
+    if (A.gather || A.nph > HP_MAXPH || (1 << (K - FR)) > (eng == ENG_I64 ? 512 : 256)) return false;
     for (int p = 0; p < A.nph; ++p)
         for (int o = A.ph[p].op_begin; o < A.ph[p].op_end; ++o) {
             const TileOp& op = A.ops[o];
@@ -1528,8 +1528,8 @@ static void hpass_i64_scaling(PassArgs<V>& A, int cin, int cout) {
 }
 
 template <typename V>
-int fused_build(int n, const std::vector<PrepOp>& ops, FusedPlan<V>& plan, bool fp_only, bool resident_ok) {
-    plan.K = fused_tile_bits(sizeof(V) == 16 ? MERA_C128 : MERA_C64, n);
+int fused_build(int n, const std::vector<PrepOp>& ops, FusedPlan<V>& plan, bool fp_only, bool resident_ok, int kforce) {
+    plan.K = kforce > 0 ? kforce : fused_tile_bits(sizeof(V) == 16 ? MERA_C128 : MERA_C64, n);
     plan.n = n;
     const int L = low_bits_for(sizeof(V) == 16 ? MERA_C128 : MERA_C64, plan.K);
     std::vector<Pass> passes = plan_passes(ops, n, plan.K, L);
@@ -1690,6 +1690,22 @@ int fused_build(int n, const std::vector<PrepOp>& ops, FusedPlan<V>& plan, bool 
             if (ok) dpass_args(A, n, plan.dargs[i]);
         }
     }
+    // A plan made only of per-tile int64 Hadamard passes (Grover-type
+    // circuits) takes 2^13-amplitude tiles (512 threads, one CTA per SM)
+    // when that saves passes: one more butterfly level per HBM round trip
+    if (sizeof(V) == 16 && kforce == 0 && plan.K == 12 && n >= 14 && !getenv("MERA_TILE_BITS")) {
+        auto all_hp = [](const FusedPlan<V>& p) {
+            bool all = !p.args.empty();
+            for (size_t i = 0; i < p.args.size() && all; ++i) all = p.single[i] < 0 && p.hpass[i] && p.eng[i] == ENG_I64;
+            return all;
+        };
+        if (all_hp(plan)) {
+            FusedPlan<V> wide;
+            if (fused_build<V>(n, ops, wide, fp_only, resident_ok, 13) == MERA_OK && all_hp(wide) &&
+                wide.args.size() < plan.args.size())
+                plan = std::move(wide);
+        }
+    }
     return MERA_OK;
 }
 
@@ -1807,8 +1823,9 @@ int fused_launch(const FusedPlan<V>& plan, size_t i, PassArgs<V>& A, unsigned ny
     if (sizeof(V) == 16 && ny == 1 && plan.hpass[i]) {
         static int sms = 0;
         if (!sms) MERA_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0));
+        const bool wide = K > 12;   // 512 threads, one CTA per SM
         const unsigned ctas =
-            (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(tiles, (uint64_t)HP_CTAS_PER_SM * (uint64_t)sms));
+            (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(tiles, (uint64_t)(wide ? 1 : 2) * (uint64_t)sms));
         HPassArgs h;
         uint64_t tilemask = 0;
         for (int b = 0; b < K; ++b) tilemask |= 1ull << A.tpos[b];
@@ -1858,7 +1875,7 @@ int fused_launch(const FusedPlan<V>& plan, size_t i, PassArgs<V>& A, unsigned ny
                 h.hrun[o] = (unsigned char)(m | (len << 4));
                 o += len;
             }
-        const void* fn = tile_fn_hpass(plan.eng[i], A.q_in ? 0 : 1, A.q_out ? 1 : 0, A.qend & 1);
+        const void* fn = tile_fn_hpass(plan.eng[i], A.q_in ? 0 : 1, A.q_out ? 1 : 0, A.qend & 1, wide ? 1 : 0);
         const size_t hsm = ((size_t)1 << K) * sizeof(V);
         MERA_TRY(opt_in_smem(fn, hsm));
         void* args[] = {reinterpret_cast<void*>(&A), &h};
@@ -1871,8 +1888,8 @@ int fused_launch(const FusedPlan<V>& plan, size_t i, PassArgs<V>& A, unsigned ny
     return launch_end(st);
 }
 
-template int fused_build<double2>(int, const std::vector<PrepOp>&, FusedPlan<double2>&, bool, bool);
-template int fused_build<float2>(int, const std::vector<PrepOp>&, FusedPlan<float2>&, bool, bool);
+template int fused_build<double2>(int, const std::vector<PrepOp>&, FusedPlan<double2>&, bool, bool, int);
+template int fused_build<float2>(int, const std::vector<PrepOp>&, FusedPlan<float2>&, bool, bool, int);
 template int fused_launch<double2>(const FusedPlan<double2>&, size_t, PassArgs<double2>&, unsigned, cudaStream_t);
 template int fused_launch<float2>(const FusedPlan<float2>&, size_t, PassArgs<float2>&, unsigned, cudaStream_t);
 

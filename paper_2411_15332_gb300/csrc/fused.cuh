@@ -27,11 +27,13 @@ struct FusedPlan {
 // fp_only: every pass in the float engine (coefficients as plain values).
 // resident_ok: a complex128 circuit of unitary gates whose mixing gates all
 // precede a monomial body may keep the state in int64 fixed point across
-// its passes (the caller then launches qscale_launch before the first pass
-// and sets PassArgs::qS).
+// its passes, and runs of Hadamard passes of any unitary circuit may keep
+// per-amplitude exponents between them (the caller then launches
+// qscale_launch before the first pass and sets PassArgs::qS).  kforce > 0
+// fixes the tile bits.
 template <typename V>
 int fused_build(int n, const std::vector<PrepOp>& ops, FusedPlan<V>& plan, bool fp_only = false,
-                bool resident_ok = false);
+                bool resident_ok = false, int kforce = 0);
 // S = 59 - floor(log2 of a bound of the norm of the complex128 state psi
 // (2^n amplitudes)); a pass with g headroom bits stores value * 2^(S - g).
 // Uses 16 KiB of scratch; S is written to scratch + 8192.

@@ -984,9 +984,10 @@ __global__ void __launch_bounds__(sizeof(SV) == 16 ? 256 : 512,
 // add of the deposited grid stride ((tb | ~M) + dG) & M over the non-tile
 // mask M.  Every pass reads through the load staging map (the planner
 // stages the loads of these passes).
-constexpr int HP_CTAS_PER_SM = 2;
 constexpr int HP_MAXPH = 8;
-constexpr int HP_THREADS = 256;    // 2^(K - FR) for K = 12 tiles (fewer for smaller K)
+// Two shapes: 256 threads (tiles of up to 2^12 amplitudes, two CTAs per SM)
+// and, for the per-tile engine, 512 threads (2^13-amplitude tiles, 128 KiB,
+// one CTA per SM: one more butterfly level per pass).
 struct HPassArgs {
     unsigned long long ntmask;     // non-tile global bits (below n)
     unsigned long long dstride;    // gridDim.x deposited into the non-tile bits
@@ -1024,10 +1025,14 @@ __device__ __forceinline__ long long shr_lt32(long long v, int k) {
 // a signed mantissa (re, im), bits 0..5 of the real word the amplitude's
 // exponent code e (0..63), bits 0..5 of the imaginary word are 0; value =
 // mantissa * 2^-(e + B), B a bias fixed per circuit from the state's norm
-// bound.  A stored amplitude has max(|re|, |im|) in [2^55, 2^56] (56
-// significant bits, more than a double's 53) unless it is below the
-// normal range, where e = 63 keeps it unnormalised (zero included).
-constexpr int EF_LZ = 8;          // leading zeros of a normalised mantissa word before the shift by 6
+// bound.  A stored amplitude has max(|re|, |im|) in [2^52, 2^53] (53
+// significant bits, as in a double) unless it is below the normal range,
+// where e = 63 keeps it unnormalised (zero included).  The mantissa sits
+// where a pass with 9 headroom bits wants the tile's largest amplitude, so
+// most amplitudes load with a shift by a few bits to the left (exact) and
+// only those below the tile's largest exponent round.
+constexpr int EF_LZ = 11;         // leading zeros of a normalised mantissa word before the shift by 6
+constexpr int EF_TOP = 53;        // |mantissa| <= 2^EF_TOP
 
 // round(v / 2^s), s >= 1 (0 for s >= 63)
 __device__ __forceinline__ long long ef_rshift(long long v, int s) {
@@ -1038,7 +1043,7 @@ __device__ __forceinline__ long long ef_rshift(long long v, int s) {
 __device__ __forceinline__ double2 ef_store(long long vx, long long vy, int T, int B) {
     const unsigned long long a = (unsigned long long)((vx < 0 ? -vx : vx) | (vy < 0 ? -vy : vy));
     if (a == 0) return make_double2(__longlong_as_double(63ll), 0.0);
-    int sl = __clzll((long long)a) - EF_LZ;     // shift that puts the top bit at 55
+    int sl = __clzll((long long)a) - EF_LZ;     // shift that puts the top bit at 52
     int e = T + sl - B;
     if (e > 63) {                               // below the normal range
         sl -= e - 63;
@@ -1072,15 +1077,15 @@ __device__ __forceinline__ void op_hmask(V (&x)[FRA], int m) {
 // pass writes that format, 0 = doubles (the last pass of a run); ODD: 0 =
 // the pass's level count to scale away is even (no 1/sqrt(2) product).  Separate instantiations keep
 // code a pass never runs out of its instruction stream.
-template <int ENG, int QIN, int QOUT, int ODD>
-__global__ void __launch_bounds__(HP_THREADS, HP_CTAS_PER_SM)
+template <int ENG, int QIN, int QOUT, int ODD, int NT = 256>
+__global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
     k_hpass(const __grid_constant__ PassArgs<double2> a, const __grid_constant__ HPassArgs h) {
     static_assert(ENG == ENG_I64 || ENG == ENG_Q, "int64 engines only");
     using V = I2;
     extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ int s_emax[HP_THREADS / 32];
-    __shared__ unsigned long long s_gloc[HP_MAXPH][HP_THREADS];
-    __shared__ short s_sb[HP_MAXPH][HP_THREADS], s_ob[HP_MAXPH][HP_THREADS];
+    __shared__ int s_emax[NT / 32];
+    __shared__ unsigned long long s_gloc[HP_MAXPH][NT];
+    __shared__ short s_sb[HP_MAXPH][NT], s_ob[HP_MAXPH][NT];
     const int K = a.K;
     const uint32_t T = 1u << (K - FR);
     const uint32_t tid = threadIdx.x;
@@ -1089,7 +1094,7 @@ __global__ void __launch_bounds__(HP_THREADS, HP_CTAS_PER_SM)
     int Sq = 0, B = 0;
     if constexpr (ENG == ENG_Q) Sq = *a.qS - a.qgi;
     // EF bias: amplitudes are below 2^(60 - *qS); code 0 holds up to 16x that
-    if constexpr (ENG == ENG_I64 && (QIN == 0 || QOUT == 1)) B = *a.qS - 8;
+    if constexpr (ENG == ENG_I64 && (QIN == 0 || QOUT == 1)) B = *a.qS - 11;
     // per phase and thread (tile-independent): global offset of register
     // slot 0, and the entry / exit slot bases in shared memory
     for (int p = 0; p < a.nph; ++p) {
@@ -1195,9 +1200,9 @@ __global__ void __launch_bounds__(HP_THREADS, HP_CTAS_PER_SM)
                     __syncthreads();
                     int emin = 63;
                     for (int w = 0; w < (int)((T + 31) >> 5); ++w) emin = min(emin, s_emax[w]);
-                    // |mantissa| <= 2^56 at code emin becomes < 2^(62 - guard)
-                    const int sh0 = a.guard - 6 - emin;
-                    S = emin + B + 6 - a.guard;
+                    // |mantissa| <= 2^EF_TOP at code emin becomes <= 2^(62 - guard)
+                    const int sh0 = a.guard - (62 - EF_TOP) - emin;
+                    S = emin + B + (62 - EF_TOP) - a.guard;
 #pragma unroll
                     for (int j = 0; j < FRA; ++j) {
                         const int sh = (int)(x[j].x & 63) + sh0;

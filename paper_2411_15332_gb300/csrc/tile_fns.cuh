@@ -17,8 +17,10 @@ const void* tile_fn_i64(int feat, int qin);
 // the Hadamard-pass kernel (ENG_I64 or ENG_Q): qin = 1 when the pass reads
 // doubles, qout = 1 when it writes the engine's own format (ENG_Q: global
 // fixed point; ENG_I64: per-amplitude exponents), odd = 1 when its level
-// count to scale away may be odd
-const void* tile_fn_hpass(int eng, int qin, int qout, int odd);
+// count to scale away may be odd, wide = 1 for 512 threads (2^13-amplitude
+// tiles, ENG_I64 only)
+const void* tile_fn_hpass(int eng, int qin, int qout, int odd, int wide);
+const void* tile_fn_hpass_wide(int qin, int qout, int odd);
 const void* tile_fn_fp(int feat, int qin);
 // the complex64 kernel
 const void* tile_fn_c64();
