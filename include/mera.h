@@ -163,7 +163,12 @@ int mera_apply_matrix(mera_state* s, const double* matrix, const int* targets, i
 /* Apply ops[0..nops-1] in order.  MERA_MODE_PER_GATE launches one kernel per
  * op; MERA_MODE_FUSED plans shared-memory tile passes that apply runs of
  * gates (and Hadamard butterflies) per HBM read/write.  All ops are
- * validated before anything is launched. */
+ * validated before anything is launched.  Launches are asynchronous: a
+ * fused pass that stages its tiles with bulk copies waits for them with a
+ * bounded wait (about a second); one that ran out is reported as
+ * MERA_ETIMEOUT, once, by the next call that synchronises the state's
+ * stream (mera_state_synchronize, mera_state_copy_to_host, the readouts),
+ * and the amplitudes are then not valid. */
 int mera_apply_circuit(mera_state* s, const mera_op* ops, size_t nops, int mode);
 
 /* Describe how MERA_MODE_FUSED would run ops[0..nops-1] on n qubits of
@@ -173,7 +178,8 @@ int mera_apply_circuit(mera_state* s, const mera_op* ops, size_t nops, int mode)
  * bits, arithmetic engine, Hadamard levels, register phases, op kinds,
  * the kernel that runs it: "stream" / "pipelined" (Hadamard-pass kernel) /
  * neither (general tile kernel), permutation runs on its loads / stores
- * ("gather" / "scatter"), and for the resident engine its scaling: levels
+ * ("gather" / "scatter"), "bulk" where the Hadamard-pass kernel stages its
+ * tiles with bulk copies of 128-byte chunks, and for the resident engine its scaling: levels
  * scaled at the end and at phase exits, headroom bits), written as a
  * NUL-terminated string into out[cap] (truncated if longer).  Host only;
  * *npasses (may be NULL) receives the number of passes. */
@@ -358,6 +364,13 @@ int mera_profile_enable(int on);
  * MERA_KCLASS_COUNT; either may be NULL).  Also returns the summed
  * algorithmic bytes the timed launches moved (bytes may be NULL). */
 int mera_profile_read(uint64_t* launches, double* ms, double* bytes);
+
+/* Test hook for the bounded waits: every bulk-staged tile of later fused
+ * launches expects `bytes` more than its copies deliver (a multiple of 16,
+ * at most 4096), so that its wait runs out and the pass reports
+ * MERA_ETIMEOUT.  0 (the default) restores normal operation.  Process-wide;
+ * MERA_EINVAL for other values. */
+int mera_test_bulk_shortfall(unsigned bytes);
 
 #ifdef __cplusplus
 }

@@ -107,6 +107,7 @@ PROTOS = {
     "mera_batch_observables": (I, [P, IP, I, I, DP]),
     "mera_adjoint_grad": (I, [P, I, I, DP, DP, DP]),
     "mera_rh_mvm": (I, [P, P, I, I, U64P]),
+    "mera_test_bulk_shortfall": (I, [C.c_uint]),
     "mera_profile_enable": (I, [I]),
     "mera_profile_read": (I, [U64P, DP, DP]),
 }

@@ -125,6 +125,25 @@ int state_ensure_scratch(mera_state* s, size_t bytes) {
     return MERA_OK;
 }
 
+int state_wait_flag(mera_state* s, int** flag) {
+    if (!s->wait_flag) {
+        MERA_CHECK_CUDA(cudaMalloc(&s->wait_flag, 256));
+        MERA_CHECK_CUDA(cudaMemsetAsync(s->wait_flag, 0, sizeof(int), s->stream));
+        MERA_CHECK_CUDA(cudaHostAlloc(&s->wait_host, sizeof(int), cudaHostAllocDefault));
+        *s->wait_host = 0;
+    }
+    *flag = s->wait_flag;
+    return MERA_OK;
+}
+
+int state_check_waits(mera_state* s) {
+    if (!s->wait_host || *s->wait_host == 0) return MERA_OK;
+    *s->wait_host = 0;
+    MERA_CHECK_CUDA(cudaMemsetAsync(s->wait_flag, 0, sizeof(int), s->stream));
+    set_error("a bounded wait for a staged tile copy ran out; the state's amplitudes are not valid");
+    return MERA_ETIMEOUT;
+}
+
 template <typename V>
 __global__ void k_set_one(V* psi, uint64_t i) {
     V one;
@@ -248,6 +267,8 @@ int mera_state_destroy(mera_state* s) {
     if (s->prog_host) cudaFreeHost(s->prog_host);
     fused_cache_free(s);
     if (s->pong) cudaFree(s->pong);
+    if (s->wait_flag) cudaFree(s->wait_flag);
+    if (s->wait_host) cudaFreeHost(s->wait_host);
     delete s;
     return MERA_OK;
     API_END
@@ -290,7 +311,7 @@ int mera_state_copy_to_host(mera_state* s, void* host) {
     MERA_RETURN_IF(host == nullptr, MERA_EINVAL, "host is NULL");
     MERA_CHECK_CUDA(cudaMemcpyAsync(host, s->data, num_amps(s) * elem_bytes(s->dtype), cudaMemcpyDeviceToHost, s->stream));
     MERA_CHECK_CUDA(cudaStreamSynchronize(s->stream));
-    return MERA_OK;
+    return state_check_waits(s);
     API_END
 }
 
@@ -305,7 +326,7 @@ int mera_state_get_amplitudes(mera_state* s, const uint64_t* idx, size_t k, doub
 int mera_state_synchronize(mera_state* s) {
     MERA_TRY(check_state(s));
     MERA_CHECK_CUDA(cudaStreamSynchronize(s->stream));
-    return MERA_OK;
+    return state_check_waits(s);
 }
 
 int mera_gate_matrix(int gate, const double* params, int* nt, double* out) {
@@ -482,6 +503,14 @@ int mera_measure(mera_state* s, const double* u, size_t k, uint64_t* idx_out) {
     MERA_TRY(check_state(s));
     MERA_RETURN_IF(k > 0 && (u == nullptr || idx_out == nullptr), MERA_EINVAL, "NULL array");
     return measure(s, u, k, idx_out);
+    API_END
+}
+
+int mera_test_bulk_shortfall(unsigned bytes) {
+    API_BEGIN
+    MERA_RETURN_IF(bytes % 16 != 0 || bytes > 4096, MERA_EINVAL, "shortfall %u: a multiple of 16 up to 4096", bytes);
+    fused_set_bulk_shortfall(bytes);
+    return MERA_OK;
     API_END
 }
 

@@ -82,6 +82,11 @@ struct mera_state {
     void* pong = nullptr;
     size_t pong_bytes = 0;
     bool pong_failed = false;
+    // status of the bounded waits in fused passes: a device int the kernels
+    // set when a wait runs out, and its pinned host copy (read after each
+    // synchronisation)
+    int* wait_flag = nullptr;
+    int* wait_host = nullptr;
 };
 
 namespace mera {
@@ -90,6 +95,11 @@ inline size_t elem_bytes(int dtype) { return dtype == MERA_C128 ? 16 : 8; }
 inline uint64_t num_amps(const mera_state* s) { return 1ull << s->n; }
 
 int state_ensure_scratch(mera_state* s, size_t bytes);
+// After a stream synchronisation: MERA_ETIMEOUT (once) if a bounded device
+// wait of a fused pass ran out since the last check, else MERA_OK.
+int state_check_waits(mera_state* s);
+// The wait-status flag (allocated on first use).
+int state_wait_flag(mera_state* s, int** flag);
 
 // ------------------------------------------------------------ gate model --
 enum GateKind { KIND_IDENTITY = 0, KIND_DIAG = 1, KIND_MONO = 2, KIND_DENSE = 3 };
@@ -126,6 +136,7 @@ int apply_fused(mera_state* s, const std::vector<PrepOp>& ops);
 // circuit of the state reuses its passes and device tables.
 int apply_fused_circuit(mera_state* s, const mera_op* ops, size_t nops);
 void fused_cache_free(mera_state* s);
+void fused_set_bulk_shortfall(unsigned bytes);
 int plan_summary(int n, int dtype, const std::vector<PrepOp>& ops, std::string* out, int* npasses);
 
 }  // namespace mera

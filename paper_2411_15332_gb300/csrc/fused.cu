@@ -22,6 +22,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+
 #include "common.cuh"
 #include "fused.cuh"
 #include "tile_fns.cuh"
@@ -38,6 +40,117 @@ int fused_tile_bits(int dtype, int n) {
     }
     if (K > n) K = n;
     return K;
+}
+
+// MERA_BULK=0 stages Hadamard-pass tiles with 16-byte asynchronous copies
+// only (no bulk copies).
+static bool bulk_enabled() {
+    static int v = -1;
+    if (v < 0) {
+        const char* e = getenv("MERA_BULK");
+        v = (e && atoi(e) == 0) ? 0 : 1;
+    }
+    return v == 1;
+}
+
+// Test hook: bytes each bulk-staged tile expects beyond what is copied, so
+// that its bounded waits run out (0 in normal use).
+static unsigned g_bulk_shortfall = 0;
+void fused_set_bulk_shortfall(unsigned bytes) { g_bulk_shortfall = bytes; }
+
+// The tensor-map dimensions of a tile for tiled tensor copies (see
+// HPassArgs): the state's amplitude bits 0..n-1 split into runs of tile
+// and non-tile bits, ascending; dimension 0 holds re/im and the tile run
+// from bit 0 (which must cover bits 0..2: rows of at least 128 bytes).
+// Box sizes are at most 256 words per dimension, so long tile runs take
+// several dimensions.  The tile's top `m` local bits may count as non-tile
+// bits: the tile is then 2^m copies, one per value of those bits.  False if
+// more than TMA_DIMS dimensions are needed.
+struct TmaDims {
+    int m;                      // top local bits iterated by separate copies (0..2)
+    uint64_t gdim[TMA_DIMS];    // extent in float64 words (dimension 0) / in steps of its lowest bit
+    uint64_t gstride[TMA_DIMS]; // bytes between consecutive coordinates (dimension 0: 8)
+    uint32_t box[TMA_DIMS];
+    unsigned char sh[TMA_DIMS];
+    unsigned mk[TMA_DIMS];
+};
+static bool tma_dims_m(const int* tpos, int K, int n, int m, TmaDims& d) {
+    bool tile[64] = {};
+    for (int b = 0; b < K - m; ++b) tile[tpos[b]] = true;
+    if (n > 40 || K - m < 3 || !tile[0] || !tile[1] || !tile[2]) return false;
+    d.m = m;
+    int nd = 0;
+    auto add = [&](int lo, int len, bool t) {
+        if (nd == TMA_DIMS) return false;
+        const uint64_t ext = (nd == 0 ? 2ull : 1ull) << len;
+        d.gdim[nd] = ext;
+        d.gstride[nd] = nd == 0 ? 8ull : (16ull << lo);
+        d.box[nd] = t ? (uint32_t)ext : 1u;
+        d.sh[nd] = (unsigned char)(t ? 0 : lo);
+        d.mk[nd] = t ? 0u : (unsigned)((1ull << len) - 1ull);
+        ++nd;
+        return true;
+    };
+    for (int q = 0; q < n;) {
+        int e = q;
+        while (e < n && tile[e] == tile[q]) ++e;
+        if (tile[q]) {
+            for (int lo = q; lo < e;) {
+                const int len = std::min(e - lo, nd == 0 ? 7 : 8);
+                if (!add(lo, len, true)) return false;
+                lo += len;
+            }
+        } else {
+            if (e - q > 31 || !add(q, e - q, false)) return false;   // coordinates are signed 32-bit
+        }
+        q = e;
+    }
+    for (; nd < TMA_DIMS; ++nd) {
+        d.gdim[nd] = 1;
+        d.gstride[nd] = 16ull << n;
+        d.box[nd] = 1;
+        d.sh[nd] = 0;
+        d.mk[nd] = 0;
+    }
+    return true;
+}
+static bool tma_dims(const int* tpos, int K, int n, TmaDims& d) {
+    for (int m = 0; m <= 2; ++m)
+        if (tma_dims_m(tpos, K, n, m, d)) return true;
+    return false;
+}
+
+// Encode the tensor map of `d` over the state at `base` (the driver's
+// encoder, found through the runtime).
+static int encode_tile_map(CUtensorMap* m, const void* base, const TmaDims& d) {
+    using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static Encode fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<Encode>(p);
+        cudaGetLastError();
+    });
+    MERA_RETURN_IF(!fn, MERA_ECUDA, "the driver's tensor-map encoder is not available");
+    cuuint64_t gdim[TMA_DIMS], gstr[TMA_DIMS - 1];
+    cuuint32_t box[TMA_DIMS], es[TMA_DIMS];
+    for (int i = 0; i < TMA_DIMS; ++i) {
+        gdim[i] = d.gdim[i];
+        box[i] = d.box[i];
+        es[i] = 1;
+        if (i > 0) gstr[i - 1] = d.gstride[i];
+    }
+    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, TMA_DIMS, const_cast<void*>(base), gdim, gstr, box, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    MERA_RETURN_IF(r != CUDA_SUCCESS, MERA_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return MERA_OK;
 }
 
 static int low_bits_for(int dtype, int K) {
@@ -1281,7 +1394,19 @@ struct PassBuilder {
                 wl[i] = 1u << i;
                 rl[i] = 1u << nonreg[0][i];
             }
-            choose_z(zin, wl, rl, 1u);
+            // natural order (identity slot map) when it costs no bank
+            // conflicts and the tile is one tiled tensor copy (rows of
+            // 128 bytes or more, at most 5 dimensions)
+            uint32_t zid[16];
+            for (int b = 0; b < 16; ++b) zid[b] = b < K ? 1u << b : 0u;
+            TmaDims td;
+            const bool tma = sizeof(V) == 16 && K >= 4 && tma_dims(A.tpos, K, n, td);
+            if (A.load_smem && tma && bulk_enabled() && deficiency(zid, wl) == 0 && deficiency(zid, rl) == 0) {
+                memcpy(zin, zid, sizeof(zin));
+                A.bulk = 1;
+            } else {
+                choose_z(zin, wl, rl, 1u);
+            }
             fill_side(A.ld, zin, stage_bits, stage_rb, nullptr);
         }
         for (int ph = 0; ph < np; ++ph) {
@@ -1618,6 +1743,8 @@ int fused_build(int n, const std::vector<PrepOp>& ops, FusedPlan<V>& plan, bool 
         }
         plan.feat[i] = (unsigned char)round_feat(plan.eng[i], b.features(), sizeof(V) == 16);
         plan.hpass[i] = hpass_ok(plan.args[i], plan.eng[i], plan.K) ? 1 : 0;
+        if (!plan.hpass[i]) plan.args[i].bulk = 0;   // only the pipelined kernel stages with bulk copies
+        plan.bulk = plan.bulk || plan.args[i].bulk;
     }
     // int64 passes on float64 storage scale their levels by 2^(-qend/2).  The
     // scale is linear, so a pass with an odd level count leaves one level (a
@@ -1838,6 +1965,22 @@ int fused_launch(const FusedPlan<V>& plan, size_t i, PassArgs<V>& A, unsigned ny
                 g >>= 1;
             }
         h.ntiles = (unsigned)tiles;
+        h.err = plan.wait_flag;
+        h.extra_tx = g_bulk_shortfall;
+        memset(h.tsh, 0, sizeof(h.tsh));
+        memset(h.tmk, 0, sizeof(h.tmk));
+        if (A.bulk) {
+            MERA_RETURN_IF(!h.err, MERA_EINVAL, "bulk-staged pass launched without a wait-status flag");
+            TmaDims td;
+            MERA_RETURN_IF(!tma_dims(A.tpos, K, plan.n, td), MERA_EINVAL, "bulk-staged pass without a tensor map");
+            MERA_TRY(encode_tile_map(&h.tmap, A.psi, td));
+            for (int d = 0; d < TMA_DIMS; ++d) {
+                h.tsh[d] = td.sh[d];
+                h.tmk[d] = td.mk[d];
+            }
+            h.tm = td.m;
+            for (int j = 0; j < 2; ++j) h.tit[j] = j < td.m ? 1ull << A.tpos[K - td.m + j] : 0ull;
+        }
         for (int ph = 0; ph < A.nph; ++ph)
             for (int r = 0; r < FR; ++r) h.gm[ph][r] = 1ull << A.tpos[A.ph[ph].rb[r]];
         // parity masks of the sign terms on the scattered store index
@@ -1943,6 +2086,7 @@ static int launch_plan(mera_state* s, FusedPlan<V>& plan, const std::vector<Prep
         const int* qS = reinterpret_cast<const int*>(reinterpret_cast<char*>(s->scratch) + 8192);
         for (PassArgs<V>& A : plan.args) A.qS = qS;
     }
+    if (plan.bulk) MERA_TRY(state_wait_flag(s, &plan.wait_flag));
     // resident runs alternate between the state and a second buffer (passes
     // out of place need no load-before-store ordering); the buffers are
     // assigned so that every run ends in the state
@@ -1987,6 +2131,9 @@ static int launch_plan(mera_state* s, FusedPlan<V>& plan, const std::vector<Prep
         }
         i = e;
     }
+    // the wait status, read by the next synchronising call
+    if (plan.bulk)
+        MERA_CHECK_CUDA(cudaMemcpyAsync(s->wait_host, s->wait_flag, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
     return MERA_OK;
 }
 
@@ -2088,7 +2235,7 @@ static int describe_fused(int n, int dtype, const std::vector<PrepOp>& ops, std:
         for (int o = 0; o < nop; ++o)
             if (A.ops[o].type == TOP_Z4) nterms += A.ops[o].aux2;
         dsep += " z4_terms=" + std::to_string(nterms) + (plan.dpass[i] ? " stream" : "") +
-                (plan.hpass[i] ? " pipelined" : "") + (A.gather ? " gather" : "") + (A.scatter ? " scatter" : "");
+                (plan.hpass[i] ? " pipelined" : "") + (A.bulk ? " bulk" : "") + (A.gather ? " gather" : "") + (A.scatter ? " scatter" : "");
         if (plan.eng[i] == ENG_Q || (plan.eng[i] == ENG_I64 && plan.hpass[i])) {
             // int64 scaling: levels scaled at phase exits (2 * shift) and at the end
             int exits = 0;

@@ -22,6 +22,8 @@ struct FusedPlan {
     bool resident = false;                // complex128 state kept as int64 fixed point (ENG_Q)
     int qguard = 0;                       // ENG_Q: headroom bits above the state norm
     bool efmt = false;                    // ENG_I64 Hadamard runs keep per-amplitude exponents between passes
+    bool bulk = false;                    // some Hadamard pass stages its tiles with bulk copies
+    int* wait_flag = nullptr;             // device int the bulk-copy waits set when they run out (set at launch)
 };
 
 // fp_only: every pass in the float engine (coefficients as plain values).

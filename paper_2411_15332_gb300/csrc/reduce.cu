@@ -255,6 +255,7 @@ int observables(mera_state* s, int q, double out[3]) {
     MERA_TRY(observables_device(s, q, partial, out_dev));
     MERA_CHECK_CUDA(cudaMemcpyAsync(out, out_dev, 3 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     MERA_CHECK_CUDA(cudaStreamSynchronize(s->stream));
+    MERA_TRY(state_check_waits(s));
     return MERA_OK;
 }
 
@@ -276,6 +277,7 @@ static int argmax_t(mera_state* s, uint64_t* idx, double* prob) {
     double res[2];
     MERA_CHECK_CUDA(cudaMemcpyAsync(res, op, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     MERA_CHECK_CUDA(cudaStreamSynchronize(s->stream));
+    MERA_TRY(state_check_waits(s));
     unsigned long long i;
     memcpy(&i, &res[1], sizeof(i));
     *idx = i;
@@ -302,6 +304,7 @@ static int measure_t(mera_state* s, const double* u, size_t k, uint64_t* out) {
     std::vector<double> hp(3 * nb);
     MERA_CHECK_CUDA(cudaMemcpyAsync(hp.data(), partial, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     MERA_CHECK_CUDA(cudaStreamSynchronize(s->stream));
+    MERA_TRY(state_check_waits(s));
     std::vector<double> cum(nb + 1, 0.0);
     for (int b = 0; b < nb; ++b) cum[b + 1] = cum[b] + hp[3 * b];
     const double total = cum[nb];
@@ -337,6 +340,7 @@ static int measure_t(mera_state* s, const double* u, size_t k, uint64_t* out) {
     std::vector<unsigned long long> res(k);
     MERA_CHECK_CUDA(cudaMemcpyAsync(res.data(), d_out, k * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s->stream));
     MERA_CHECK_CUDA(cudaStreamSynchronize(s->stream));
+    MERA_TRY(state_check_waits(s));
     for (size_t j = 0; j < k; ++j) out[j] = res[j];
     return MERA_OK;
 }
@@ -359,6 +363,7 @@ static int gather_t(mera_state* s, const uint64_t* idx, size_t k, double* out) {
     MERA_TRY(launch_end(s->stream));
     MERA_CHECK_CUDA(cudaMemcpyAsync(out, d_out, k * sizeof(double2), cudaMemcpyDeviceToHost, s->stream));
     MERA_CHECK_CUDA(cudaStreamSynchronize(s->stream));
+    MERA_TRY(state_check_waits(s));
     return MERA_OK;
 }
 

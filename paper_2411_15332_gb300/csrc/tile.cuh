@@ -41,6 +41,7 @@
 // (TOP_DSEP).
 #pragma once
 
+#include <cuda.h>   // CUtensorMap (the type only; maps are encoded on the host)
 #include <type_traits>
 
 #include "kernels.cuh"
@@ -172,6 +173,7 @@ struct PassArgs {
     XSide ld;            // load staging: slot of element tid + i * 2^(K-FR)
     XSide st;            // store staging: the same for the final copy out
     int gather, scatter; // 1: phase 0 loads through gin / the last phase stores through gout
+    int bulk;            // Hadamard-pass kernel: 1 = the load staging is in natural chunk order (bulk copies)
     GMap gin, gout;      // (a permutation at the start / end of the pass rides on the addresses)
     int8_t ntq[TILE_MAX_NT];   // global positions of separable non-tile factors
     TilePhase ph[TILE_MAX_PHASES];
@@ -988,7 +990,22 @@ constexpr int HP_MAXPH = 8;
 // Two shapes: 256 threads (tiles of up to 2^12 amplitudes, two CTAs per SM)
 // and, for the per-tile engine, 512 threads (2^13-amplitude tiles, 128 KiB,
 // one CTA per SM: one more butterfly level per pass).
+// Tiled tensor copies of a tile (PassArgs::bulk): the state as a tensor
+// of float64 words of at most 5 dimensions in ascending global bit order,
+// each dimension a run of tile bits (the box spans it) or of non-tile bits
+// (box 1, coordinate from the tile base); the first holds re/im and the
+// tile's lowest bits.  The tile's top `tm` local bits may be taken as
+// non-tile bits, one copy per value (2^tm copies of 2^(K-tm) amplitudes).
+// Smem then holds the tile in natural local order.
+constexpr int TMA_DIMS = 5;
 struct HPassArgs {
+    CUtensorMap tmap;              // encoded per launch on the host (input buffer of the pass)
+    int* err;                      // set to 1 when a bounded wait for a tile copy ran out
+    unsigned extra_tx;             // bytes expected per tile beyond the tile (0; a test makes waits run out)
+    unsigned char tsh[TMA_DIMS];   // coordinate i = (copy base >> tsh[i]) & tmk[i]
+    unsigned tmk[TMA_DIMS];
+    int tm;                        // copies per tile: 2^tm
+    unsigned long long tit[2];     // global bits of the copies' local bits K-tm, K-tm+1
     unsigned long long ntmask;     // non-tile global bits (below n)
     unsigned long long dstride;    // gridDim.x deposited into the non-tile bits
     unsigned ntiles;
@@ -1011,6 +1028,46 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Tensor-memory-access copies, completed in bytes on an mbarrier.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void tma_load5(void* sdst, const CUtensorMap* map, const int (&c)[5], unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+        "%6}], [%7];\n" ::"r"(smem_u32(sdst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4]),
+        "r"(smem_u32(bar))
+        : "memory");
+}
+// Bounded wait for an mbarrier phase: false if it did not complete within
+// about a second of SM clock.
+constexpr long long MBAR_WAIT_CYCLES = 1ll << 31;
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > MBAR_WAIT_CYCLES) return false;
+    return true;
 }
 
 // (hi:lo) >> k for 0 <= k < 32 (arithmetic): two funnel shifts
@@ -1082,7 +1139,8 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
     k_hpass(const __grid_constant__ PassArgs<double2> a, const __grid_constant__ HPassArgs h) {
     static_assert(ENG == ENG_I64 || ENG == ENG_Q, "int64 engines only");
     using V = I2;
-    extern __shared__ __align__(16) unsigned char smraw[];
+    extern __shared__ __align__(128) unsigned char smraw_h[];   // a tensor copy's destination: 128-byte aligned
+    unsigned char* const smraw = smraw_h;
     __shared__ int s_emax[NT / 32];
     __shared__ unsigned long long s_gloc[HP_MAXPH][NT];
     __shared__ short s_sb[HP_MAXPH][NT], s_ob[HP_MAXPH][NT];
@@ -1131,7 +1189,34 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
     auto madd = [&](uint64_t tb) { return ((tb | ~h.ntmask) + h.dstride) & h.ntmask; };
     double2* const sms = reinterpret_cast<double2*>(smraw);
     V* const sm = reinterpret_cast<V*>(smraw);
+    // Bulk staging (a.bulk: the load staging is the natural local order):
+    // one tiled tensor copy per tile, issued by thread 0 and counted in
+    // bytes on an mbarrier whose phase flips per tile.  Otherwise 16-byte
+    // asynchronous copies per element into the swizzled staging layout.
+    __shared__ unsigned long long s_bar;
+    const bool bulk = a.bulk != 0;
+    if (bulk) {
+        if (tid == 0) {
+            mbar_init(&s_bar, 1);
+            mbar_fence_init();
+        }
+    }
+    unsigned bpar = 0;
     auto prefetch = [&](uint64_t t, uint64_t tb) {
+        if (bulk) {
+            if (t < h.ntiles && tid == 0) {
+                fence_proxy_async_smem();   // the buffer's earlier reads (ordered by the barrier) come first
+                mbar_expect_tx(&s_bar, (T << 8) + h.extra_tx);
+                for (int j = 0; j < (1 << h.tm); ++j) {
+                    const uint64_t cb = tb | ((j & 1) ? h.tit[0] : 0ull) | ((j & 2) ? h.tit[1] : 0ull);
+                    int c[TMA_DIMS];
+#pragma unroll
+                    for (int i = 0; i < TMA_DIMS; ++i) c[i] = (int)((unsigned)(cb >> h.tsh[i]) & h.tmk[i]);
+                    tma_load5(sms + ((size_t)j << (K - h.tm)), &h.tmap, c, &s_bar);
+                }
+            }
+            return;
+        }
         if (t < h.ntiles) {
             const uint64_t g0 = tb | gt;
 #pragma unroll
@@ -1143,7 +1228,19 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
     __syncthreads();
     prefetch(blockIdx.x, tb);
     for (uint64_t tile = blockIdx.x; tile < h.ntiles; tile += G) {
-        cp_async_wait<0>();
+        if (bulk) {
+            // every thread waits for the tile's bytes (bounded); a wait that
+            // runs out anywhere makes the whole CTA report it and return
+            const bool ok = mbar_wait(&s_bar, bpar);
+            bpar ^= 1u;
+            if (__syncthreads_or(ok ? 0 : 1)) {
+                if (tid == 0) atomicExch(h.err, 1);
+                mbar_wait(&s_bar, bpar ^ 1u);   // give copies still in flight a bounded time to land
+                return;
+            }
+        } else {
+            cp_async_wait<0>();
+        }
         __syncthreads();   // this tile is in the buffer
         const uint64_t tbn = madd(tb);
         V x[FRA];
@@ -1384,7 +1481,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
         }
         tb = tbn;
     }
-    cp_async_wait<0>();
+    if (!bulk) cp_async_wait<0>();
 }
 
 // ------------------------------------------------ single-phase tables --

@@ -70,3 +70,69 @@ def test_small_then_full_tiles():
         got = s.to_numpy()
         s.close()
         assert max_err(got, sv.simulate(n, ops)) <= 1e-13
+
+
+def test_bulk_staging_matches_element_copies(tmp_path):
+    """Tiles staged by bulk copies of whole 128-byte chunks (natural order in
+    shared memory) give the same bits as 16-byte asynchronous copies into a
+    swizzled layout (a process with MERA_BULK=0), and both match the oracle."""
+    import os
+    import subprocess
+    import sys
+    n = 20
+    ops, _ = inputs.grover_circuit(n, 2, seed=3)
+    head, tile = _pipelined(n, ops)
+    assert sum(" bulk" in l for l in tile) >= len(tile) // 2
+    s = new_state(n)
+    s.apply_circuit(ops, mode="fused")
+    got = s.to_numpy()
+    s.close()
+    out = tmp_path / "elementwise.npy"
+    code = ("import numpy as np\n"
+            "from paper_2411_15332_gb300 import inputs, core\n"
+            f"ops, _ = inputs.grover_circuit({n}, 2, seed=3)\n"
+            f"assert ' bulk' not in core.plan_summary({n}, ops)\n"
+            f"s = core.State({n})\n"
+            "s.apply_circuit(ops, mode='fused')\n"
+            f"np.save({str(out)!r}, s.to_numpy())\n")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    subprocess.run([sys.executable, "-c", code], cwd=root, env={**os.environ, "MERA_BULK": "0"}, check=True,
+                   timeout=600)
+    ref = np.load(out)
+    assert np.array_equal(got.view(np.uint64), ref.view(np.uint64))
+    assert max_err(got, sv.simulate(n, ops)) <= 1e-13
+
+
+def test_bulk_wait_runs_out_and_is_reported():
+    """Failure detection of the bulk staging: with a test hook every tile
+    expects 16 bytes more than its copies deliver, so each CTA's bounded
+    wait runs out (about a second), sets the status flag and returns.  The
+    next synchronising call reports MERA_ETIMEOUT once; the context and the
+    state stay usable and a normal run afterwards matches the oracle."""
+    from paper_2411_15332_gb300 import _lib as L
+    n = 16
+    ops = [op("H", (q,)) for q in list(range(4, 12)) + [0]]
+    head, tile = _pipelined(n, ops)
+    assert len(tile) == 1 and " bulk" in tile[0]
+    s = new_state(n)
+    L.check(L.lib().mera_test_bulk_shortfall(16))
+    try:
+        s.apply_circuit(ops, mode="fused")
+        with pytest.raises(L.MeraError) as e:
+            s.synchronize()
+        assert e.value.code == L.MERA_ETIMEOUT
+    finally:
+        L.check(L.lib().mera_test_bulk_shortfall(0))
+    s.synchronize()   # reported once
+    s.set_basis(0)
+    s.apply_circuit(ops, mode="fused")
+    got = s.to_numpy()
+    s.close()
+    assert max_err(got, sv.simulate(n, ops)) <= 1e-13
+
+
+def test_bulk_shortfall_hook_validates():
+    from paper_2411_15332_gb300 import _lib as L
+    assert L.lib().mera_test_bulk_shortfall(8) == L.MERA_EINVAL
+    assert L.lib().mera_test_bulk_shortfall(8192) == L.MERA_EINVAL
+    assert L.lib().mera_test_bulk_shortfall(0) == L.MERA_OK

@@ -215,3 +215,20 @@ def test_hadamard_kernel_eligibility(core):
     summary = core.plan_summary(30, inputs.layered_circuit(30, 20, seed=2)).splitlines()[1:]
     hp = [l for l in summary if "pipelined" in l]
     assert len(hp) == 3 and all("scatter" in l and "gather" not in l for l in hp)
+
+
+def test_bulk_staging_eligibility(core):
+    """Hadamard passes stage their tiles with bulk copies of 128-byte chunks
+    when the tile holds the state's low three bits and phase 0 reads the
+    natural layout without bank conflicts (no register bit among local bits
+    0..2); only the pipelined kernel does."""
+    ops, _ = inputs.grover_circuit(33, 8, seed=3)
+    passes = core.plan_summary(33, ops).splitlines()[1:]
+    bulk = [p for p in passes if " bulk" in p]
+    assert len(bulk) >= 40
+    for p in bulk:
+        assert "pipelined" in p and "tile={0,1,2," in p
+    # pass 0 starts with H on qubits 0..3: phase 0 has register bits 0..2
+    assert " bulk" not in passes[0]
+    for p in core.plan_summary(30, inputs.layered_circuit(30, 20, seed=2)).splitlines()[1:]:
+        assert " bulk" not in p or "pipelined" in p
