@@ -240,7 +240,8 @@ def _dominant(table):
     return max(table, key=lambda k: table[k]["ms"]) if table else None
 
 
-KERNEL_NAMES = {"dpass": "k_dpass (streaming single-phase table pass)",
+KERNEL_NAMES = {"amp": "k_amp (monomial run pass: affine permutation gather, diagonal tables)",
+                "dpass": "k_dpass (streaming single-phase table pass)",
                 "hpass": "k_hpass (Hadamard pass: butterflies, sign terms)",
                 "tile": "k_tile (general tile pass)",
                 "gate_diag": "k_diag / k_phase (per-gate diagonal)",

@@ -177,7 +177,10 @@ int mera_apply_circuit(mera_state* s, const mera_op* ops, size_t nops, int mode)
  * then one line per tile pass (tile
  * bits, arithmetic engine, Hadamard levels, register phases, op kinds,
  * the kernel that runs it: "stream" / "pipelined" (Hadamard-pass kernel) /
- * neither (general tile kernel), permutation runs on its loads / stores
+ * "amp" (a run of affine permutation gates then diagonal gates as one
+ * monomial operator, gathered from the whole state; its index-map offsets,
+ * table selection bits and sign terms follow) / neither (general tile
+ * kernel), permutation runs on its loads / stores
  * ("gather" / "scatter"), "bulk" where the Hadamard-pass kernel stages its
  * tiles with bulk copies of 128-byte chunks, and for the resident engine its scaling: levels
  * scaled at the end and at phase exits, headroom bits), written as a
@@ -354,7 +357,8 @@ int mera_adjoint_grad(mera_batch* b, int nslots, int L, const double* theta, dou
 #define MERA_KCLASS_GATE_DIAG 7 /* per-gate diagonal kernels (phases, sign flips) */
 #define MERA_KCLASS_GATE_1Q 8   /* per-gate one-target kernels (2x2 and swaps with phases) */
 #define MERA_KCLASS_RH 9        /* the paper's RH sign-method MVM kernels */
-#define MERA_KCLASS_COUNT 10
+#define MERA_KCLASS_AMP 10      /* monomial run pass (permutation gather and diagonal tables) */
+#define MERA_KCLASS_COUNT 11
 
 /* Turn CUDA-event timing of every launch on/off (process-wide) and clear
  * the accumulated figures. */

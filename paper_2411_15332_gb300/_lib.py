@@ -18,9 +18,9 @@ MERA_OK, MERA_EINVAL, MERA_ENOMEM, MERA_EUNSUPPORTED, MERA_ECUDA, MERA_ETIMEOUT 
 MERA_C64, MERA_C128 = 0, 1
 MODE_PER_GATE, MODE_FUSED = 0, 1
 (KCLASS_GATE, KCLASS_TILE, KCLASS_REDUCE, KCLASS_DAX, KCLASS_QNN, KCLASS_HPASS, KCLASS_DPASS,
- KCLASS_GATE_DIAG, KCLASS_GATE_1Q, KCLASS_RH) = range(10)
-KCLASS_COUNT = 10
-KCLASS_NAMES = ("gate", "tile", "reduce", "dax", "qnn", "hpass", "dpass", "gate_diag", "gate_1q", "rh")
+ KCLASS_GATE_DIAG, KCLASS_GATE_1Q, KCLASS_RH, KCLASS_AMP) = range(11)
+KCLASS_COUNT = 11
+KCLASS_NAMES = ("gate", "tile", "reduce", "dax", "qnn", "hpass", "dpass", "gate_diag", "gate_1q", "rh", "amp")
 
 GATES = ["I", "X", "Y", "Z", "H", "S", "SDG", "T", "TDG", "SX", "SXDG", "P", "RX", "RY", "RZ",
          "R", "U2", "U", "SWAP", "ISWAP", "DCX", "ECR", "RXX", "RYY", "RZZ", "RZX", "FLIP", "MATRIX"]

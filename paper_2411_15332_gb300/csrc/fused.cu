@@ -168,6 +168,7 @@ struct Pass {
     uint64_t tile_mask = 0;
     std::vector<int> ops;
     int single = -1;     // >= 0: run this op with the per-gate kernel instead
+    bool amp = false;    // an affine monomial run (one streaming pass, see AmpRun)
 };
 
 // Three-target non-diagonal gates are not fused: they split the circuit and
@@ -232,7 +233,7 @@ static int diag_qubit(const PrepOp& P) {
 static void sink_diagonals(const std::vector<PrepOp>& ops, std::vector<Pass>& passes) {
     const int np = (int)passes.size();
     for (int i = 0; i < np; ++i) {
-        if (passes[i].single >= 0) continue;
+        if (passes[i].single >= 0 || passes[i].amp) continue;
         std::vector<int> keep;
         std::vector<std::pair<int, int>> moved;   // (op, target pass)
         for (size_t k = 0; k < passes[i].ops.size(); ++k) {
@@ -251,6 +252,10 @@ static void sink_diagonals(const std::vector<PrepOp>& ops, std::vector<Pass>& pa
             }
             int dest = -1;
             for (int j = i + 1; j < np && !blocked; ++j) {
+                if (passes[j].amp) {   // its permutations move qubits: stop here
+                    blocked = true;
+                    break;
+                }
                 if (passes[j].single >= 0) {
                     const PrepOp& G = ops[passes[j].single];
                     if (op_targets(G) & bit) blocked = true;
@@ -281,11 +286,209 @@ static void sink_diagonals(const std::vector<PrepOp>& ops, std::vector<Pass>& pa
     }
 }
 
-static std::vector<Pass> plan_passes(const std::vector<PrepOp>& ops, int n, int K, int L) {
+// ------------------------------------------------ affine monomial runs --
+// DAX products (Sec. III-A): the product of monomial matrices is monomial,
+// so a run of permutation gates followed by diagonal gates is one operator
+// with one nonzero per row, out[i] = D(i) in[F^-1(i)].  For permutations
+// that are affine maps of the index bits over GF(2) (X, CNOT, SWAP, and any
+// permutation of two qubits), F(j) = M j ^ c; D collects the diagonals,
+// which no permutation of the run follows, as a function of the output
+// index: per-qubit factors lam[q][bit] and patterns on several qubits.
+
+// The new index of old index x under a monomial gate's permutation (row s
+// of the gate reads column perm[s]: old pattern perm[s] moves to s).
+static uint64_t mono_apply(const PrepOp& P, uint64_t x) {
+    if ((x & P.cmask) != P.cvals) return x;
+    int s = 0;
+    for (int m = 0; m < P.k; ++m) s = (s << 1) | (int)((x >> P.t[m]) & 1ull);
+    int sn = s;
+    for (int r = 0; r < (1 << P.k); ++r)
+        if (P.perm[r] == s) {
+            sn = r;
+            break;
+        }
+    for (int m = 0; m < P.k; ++m) {
+        const uint64_t bit = (uint64_t)((sn >> (P.k - 1 - m)) & 1);
+        x = (x & ~(1ull << P.t[m])) | (bit << P.t[m]);
+    }
+    return x;
+}
+// A pure permutation gate (every value 1) whose index map is affine.
+static bool mono_affine(const PrepOp& P) {
+    if (P.kind != KIND_MONO || P.bslot >= 0) return false;
+    for (int s = 0; s < (1 << P.k); ++s)
+        if (P.v[s] != cplx(1, 0)) return false;
+    int sup[64], m = 0;
+    for (int j = 0; j < P.k; ++j) sup[m++] = P.t[j];
+    for (int q = 0; q < 64; ++q)
+        if ((P.cmask >> q) & 1ull) sup[m++] = q;
+    if (m > 6) return false;
+    auto vec = [&](int u) {
+        uint64_t x = 0;
+        for (int b = 0; b < m; ++b)
+            if ((u >> b) & 1) x |= 1ull << sup[b];
+        return x;
+    };
+    const uint64_t g0 = mono_apply(P, 0);
+    for (int u = 0; u < (1 << m); ++u)
+        for (int w = u + 1; w < (1 << m); ++w)
+            if ((mono_apply(P, vec(u) ^ vec(w)) ^ g0) != (mono_apply(P, vec(u)) ^ mono_apply(P, vec(w))))
+                return false;
+    return true;
+}
+
+static int phase_code_f(cplx v);
+static uint32_t unit_exp(cplx v);
+
+struct AmpTerm {
+    uint64_t mask, vals;   // applies where (i & mask) == vals
+    cplx v;
+};
+struct AmpRun {
+    int n = 0;
+    uint64_t col[64];      // M e_b
+    uint64_t c = 0;
+    cplx lam[64][2];
+    cplx konst = 1;
+    std::vector<AmpTerm> terms;
+    std::vector<int> ops;
+    bool diag = false;     // a diagonal was taken: no permutation may follow
+    uint64_t touched = 0;
+    explicit AmpRun(int nn) : n(nn) {
+        for (int b = 0; b < 64; ++b) {
+            col[b] = 1ull << b;
+            lam[b][0] = lam[b][1] = 1;
+        }
+    }
+    // take gate idx if the run stays one affine monomial operator
+    bool take(const std::vector<PrepOp>& all, int idx) {
+        const PrepOp& P = all[idx];
+        if (P.kind == KIND_MONO) {
+            if (diag || !mono_affine(P)) return false;
+            const uint64_t g0 = mono_apply(P, 0);
+            for (int b = 0; b < n; ++b) col[b] = mono_apply(P, col[b]) ^ g0;
+            c = mono_apply(P, c);
+        } else if (P.kind == KIND_DIAG && P.bslot < 0) {
+            diag = true;
+            uint64_t tm = 0;
+            for (int j = 0; j < P.k; ++j) tm |= 1ull << P.t[j];
+            for (int sp = 0; sp < (1 << P.k); ++sp) {
+                const cplx v = P.v[sp];
+                if (v == cplx(1, 0)) continue;
+                uint64_t vals = P.cvals;
+                for (int j = 0; j < P.k; ++j)
+                    if ((sp >> (P.k - 1 - j)) & 1) vals |= 1ull << P.t[j];
+                const uint64_t mask = P.cmask | tm;
+                if (mask == 0) konst *= v;
+                else if (popc(mask) == 1) lam[__builtin_ctzll(mask)][vals ? 1 : 0] *= v;
+                else terms.push_back(AmpTerm{mask, vals, v});
+            }
+        } else {
+            return false;
+        }
+        ops.push_back(idx);
+        touched |= op_qubits(P);
+        return true;
+    }
+};
+
+// Placement of a run's diagonal: local bits 0..11 (table A, with up to
+// AMP_A_SEL selected tile bits), table T over other tile bits (one factor
+// per tile), exact sign terms per tile or per amplitude.  False if the run
+// does not fit (then it is shortened).
+struct AmpLayout {
+    uint64_t selA = 0, tdom = 0;
+    std::vector<int> inA, inT, tileZ, elemZ;   // term indices
+};
+static bool amp_layout(const AmpRun& r, AmpLayout& L) {
+    const uint64_t LOC = 0xFFFull;
+    L = AmpLayout();
+    auto z4 = [](cplx v) { return phase_code_f(v) <= 3; };
+    // tile bits of mixed (local and tile) terms: general phases must be
+    // selected by table A; exact ones preferably, else per amplitude
+    uint64_t must = 0;
+    int freq[64] = {0};
+    for (const AmpTerm& t : r.terms) {
+        const uint64_t tm = t.mask & ~LOC;
+        if ((t.mask & LOC) && tm) {
+            if (!z4(t.v)) must |= tm;
+            else
+                for (int q = 0; q < 64; ++q)
+                    if ((tm >> q) & 1ull) ++freq[q];
+        }
+    }
+    if (popc(must) > AMP_A_SEL) return false;
+    L.selA = must;
+    while (popc(L.selA) < AMP_A_SEL) {
+        int best = -1;
+        for (int q = 12; q < r.n; ++q)
+            if (!((L.selA >> q) & 1ull) && freq[q] > 0 && (best < 0 || freq[q] > freq[best])) best = q;
+        if (best < 0) break;
+        L.selA |= 1ull << best;
+    }
+    for (int q = 12; q < r.n; ++q)
+        if (!((L.selA >> q) & 1ull) && (r.lam[q][0] != cplx(1, 0) || r.lam[q][1] != cplx(1, 0))) L.tdom |= 1ull << q;
+    for (size_t i = 0; i < r.terms.size(); ++i) {
+        const AmpTerm& t = r.terms[i];
+        const uint64_t tm = t.mask & ~LOC;
+        if (!(tm & ~L.selA)) L.inA.push_back((int)i);
+        else if (t.mask & LOC) {
+            if (!z4(t.v)) return false;
+            L.elemZ.push_back((int)i);
+        } else if (!z4(t.v)) {
+            L.tdom |= tm;
+            L.inT.push_back((int)i);
+        }
+    }
+    // exact tile-only terms: in T when its bits are there, else per tile
+    for (size_t i = 0; i < r.terms.size(); ++i) {
+        const AmpTerm& t = r.terms[i];
+        const uint64_t tm = t.mask & ~LOC;
+        if ((t.mask & LOC) || !(tm & ~L.selA) || !z4(t.v)) continue;
+        if (!(tm & ~L.tdom)) L.inT.push_back((int)i);
+        else L.tileZ.push_back((int)i);
+    }
+    return popc(L.tdom) <= AMP_T_BITS && (int)L.elemZ.size() <= AMP_MAX_Z4 && (int)L.tileZ.size() <= AMP_MAX_TZ4;
+}
+
+// The longest affine monomial run starting at ops[pos], shortened until
+// its diagonal fits the layout.
+static AmpRun amp_grow(const std::vector<PrepOp>& ops, const std::vector<int>& order, size_t pos, int n) {
+    AmpRun r(n);
+    for (size_t k = pos; k < order.size(); ++k) {
+        AmpRun next = r;
+        if (!next.take(ops, order[k])) break;
+        AmpLayout L;
+        if (!amp_layout(next, L)) break;
+        r = std::move(next);
+    }
+    return r;
+}
+// Worth a pass of its own: the run reaches more qubits than a tile pass
+// holds beside its row bits, with a few gates at least.
+static bool amp_worth(const AmpRun& r, int K) { return r.ops.size() >= 4 && popc(r.touched) > K - 3; }
+
+static std::vector<Pass> plan_passes(const std::vector<PrepOp>& ops, int n, int K, int L, bool amp_ok) {
     std::vector<Pass> passes;
     std::vector<int> seg;
-    for (int i = 0; i < (int)ops.size(); ++i) {
-        if (ops[i].kind == KIND_IDENTITY) continue;
+    std::vector<int> order;
+    for (int i = 0; i < (int)ops.size(); ++i)
+        if (ops[i].kind != KIND_IDENTITY) order.push_back(i);
+    for (size_t k = 0; k < order.size(); ++k) {
+        const int i = order[k];
+        if (amp_ok && (ops[i].kind == KIND_MONO || ops[i].kind == KIND_DIAG)) {
+            AmpRun r = amp_grow(ops, order, k, n);
+            if (amp_worth(r, K)) {
+                plan_segment(ops, seg, n, K, L, passes);
+                seg.clear();
+                Pass a;
+                a.amp = true;
+                a.ops = r.ops;
+                passes.push_back(a);
+                k += r.ops.size() - 1;
+                continue;
+            }
+        }
         if (is_barrier(ops[i])) {
             plan_segment(ops, seg, n, K, L, passes);
             seg.clear();
@@ -1601,6 +1804,155 @@ static void dpass_args(const PassArgs<V>& A, int n, DPassArgs& d) {
     d.shift = A.q_out ? A.qgo - A.qgi : 0;
 }
 
+// The streaming pass of an affine monomial run: the inverse index map
+// F^-1 (over GF(2), Gauss-Jordan), the diagonal's tables (appended to tabs,
+// split Q61 limbs) and its sign terms.
+template <typename V>
+static int amp_build(const std::vector<PrepOp>& ops, const std::vector<int>& run_ops, int n, std::vector<V>& tabs,
+                     AmpArgs& a) {
+    AmpRun r(n);
+    for (int idx : run_ops) MERA_RETURN_IF(!r.take(ops, idx), MERA_EUNSUPPORTED, "op %d left its monomial run", idx);
+    AmpLayout L;
+    MERA_RETURN_IF(!amp_layout(r, L), MERA_EUNSUPPORTED, "monomial run's diagonal does not fit its tables");
+    memset(&a, 0, sizeof(a));
+    // M^-1: rows of M, augmented with the identity
+    uint64_t row[64], inv[64];
+    for (int i = 0; i < n; ++i) {
+        row[i] = 0;
+        for (int b = 0; b < n; ++b)
+            if ((r.col[b] >> i) & 1ull) row[i] |= 1ull << b;
+        inv[i] = 1ull << i;
+    }
+    for (int b = 0; b < n; ++b) {
+        int piv = -1;
+        for (int i = b; i < n; ++i)
+            if ((row[i] >> b) & 1ull) {
+                piv = i;
+                break;
+            }
+        MERA_RETURN_IF(piv < 0, MERA_EINVAL, "monomial run's index map is not invertible");
+        std::swap(row[b], row[piv]);
+        std::swap(inv[b], inv[piv]);
+        for (int i = 0; i < n; ++i)
+            if (i != b && ((row[i] >> b) & 1ull)) {
+                row[i] ^= row[b];
+                inv[i] ^= inv[b];
+            }
+    }
+    // inv[i] is row i of M^-1
+    auto minv = [&](uint64_t v) {
+        uint64_t y = 0;
+        for (int i = 0; i < n; ++i)
+            if (popc(inv[i] & v) & 1) y |= 1ull << i;
+        return y;
+    };
+    a.in_c = minv(r.c);
+    for (int t = 0; t < DPASS_TBITS; ++t) a.in_t[t] = minv(1ull << t);
+    for (int q = 0; q < DPASS_RBITS; ++q) a.in_r[q] = minv(1ull << (DPASS_TBITS + q));
+    for (int q = 12; q < n; ++q) {
+        const uint64_t w = minv(1ull << q) ^ (1ull << q);
+        if (!w) continue;
+        MERA_RETURN_IF(a.in_nq >= AMP_MAX_XOFF, MERA_EUNSUPPORTED, "monomial run map too wide");
+        a.in_q[a.in_nq] = (int8_t)q;
+        a.in_w[a.in_nq] = w;
+        ++a.in_nq;
+    }
+    // table A: local bits 0..11 and the selected tile bits
+    int sq[AMP_A_SEL], ns = 0;
+    for (int q = 12; q < n; ++q)
+        if ((L.selA >> q) & 1ull) sq[ns++] = q;
+    a.a_nt = ns;
+    for (int f = 0; f < ns; ++f) a.a_q[f] = (int8_t)sq[f];
+    auto sel_of = [&](uint64_t idx, const int* qs, int nq) {
+        uint32_t v = 0;
+        for (int f = 0; f < nq; ++f) v |= (uint32_t)((idx >> qs[f]) & 1ull) << f;
+        return v;
+    };
+    auto spread = [&](uint32_t v, const int* qs, int nq) {
+        uint64_t x = 0;
+        for (int f = 0; f < nq; ++f)
+            if ((v >> f) & 1u) x |= 1ull << qs[f];
+        return x;
+    };
+    const bool hasT = L.tdom != 0;
+    std::vector<cplx> aloc(4096), asel((size_t)1 << ns);
+    for (uint32_t l = 0; l < 4096; ++l) {
+        cplx d = hasT ? cplx(1, 0) : r.konst;
+        for (int b = 0; b < 12; ++b) d *= r.lam[b][(l >> b) & 1];
+        aloc[l] = d;
+    }
+    for (uint32_t v = 0; v < (1u << ns); ++v) {
+        cplx d = 1;
+        for (int f = 0; f < ns; ++f) d *= r.lam[sq[f]][(v >> f) & 1];
+        asel[v] = d;
+    }
+    std::vector<int> mixed;
+    for (int ti : L.inA) {
+        const AmpTerm& t = r.terms[ti];
+        if (!(t.mask & ~0xFFFull)) {
+            for (uint32_t l = 0; l < 4096; ++l)
+                if ((l & t.mask) == t.vals) aloc[l] *= t.v;
+        } else if (!(t.mask & 0xFFFull)) {
+            for (uint32_t v = 0; v < (1u << ns); ++v)
+                if ((spread(v, sq, ns) & t.mask) == t.vals) asel[v] *= t.v;
+        } else {
+            mixed.push_back(ti);
+        }
+    }
+    a.a_off = (int)tabs.size();
+    tabs.resize(tabs.size() + ((size_t)4096 << ns));
+    for (uint32_t v = 0; v < (1u << ns); ++v) {
+        const uint64_t hi = spread(v, sq, ns);
+        for (uint32_t l = 0; l < 4096; ++l) {
+            cplx d = aloc[l] * asel[v];
+            for (int ti : mixed) {
+                const AmpTerm& t = r.terms[ti];
+                if (((hi | l) & t.mask) == t.vals) d *= t.v;
+            }
+            tabs[a.a_off + ((size_t)v << 12) + l] = PassBuilder<V>::enc_split(d);
+        }
+    }
+    // table T: the other tile bits with factors (one value per tile)
+    a.t_off = -1;
+    if (hasT) {
+        int tq[AMP_T_BITS], nt = 0;
+        for (int q = 12; q < n; ++q)
+            if ((L.tdom >> q) & 1ull) tq[nt++] = q;
+        a.t_nt = nt;
+        for (int f = 0; f < nt; ++f) a.t_q[f] = (int8_t)tq[f];
+        a.t_off = (int)tabs.size();
+        tabs.resize(tabs.size() + ((size_t)1 << nt));
+        for (uint32_t v = 0; v < (1u << nt); ++v) {
+            const uint64_t x = spread(v, tq, nt);
+            cplx d = r.konst;
+            for (int f = 0; f < nt; ++f) d *= r.lam[tq[f]][(v >> f) & 1];
+            for (int ti : L.inT) {
+                const AmpTerm& t = r.terms[ti];
+                if ((x & t.mask) == t.vals) d *= t.v;
+            }
+            tabs[a.t_off + v] = PassBuilder<V>::enc_split(d);
+        }
+        (void)sel_of;
+    }
+    for (int ti : L.tileZ) {
+        const AmpTerm& t = r.terms[ti];
+        a.tz[a.ntz].mask = t.mask;
+        a.tz[a.ntz].vals = t.vals;
+        a.tz[a.ntz].e = (int16_t)unit_exp(t.v);
+        ++a.ntz;
+    }
+    for (int ti : L.elemZ) {
+        const AmpTerm& t = r.terms[ti];
+        a.z4[a.nz].mask = t.mask;
+        a.z4[a.nz].vals = t.vals;
+        a.z4[a.nz].e = (int16_t)unit_exp(t.v);
+        ++a.nz;
+    }
+    a.ntiles = (uint32_t)(1ull << (n - 12));
+    for (int idx : run_ops) (ops[idx].kind == KIND_MONO ? a.nperm : a.ndiag) += 1;
+    return MERA_OK;
+}
+
 // A complex128 int64-engine pass of butterflies and sign terms only (a
 // closing permutation run may ride on its stores; none on its loads): the
 // Hadamard-pass kernel.
@@ -1653,18 +2005,13 @@ static void hpass_i64_scaling(PassArgs<V>& A, int cin, int cout) {
 }
 
 template <typename V>
-int fused_build(int n, const std::vector<PrepOp>& ops, FusedPlan<V>& plan, bool fp_only, bool resident_ok, int kforce) {
+int fused_build(int n, const std::vector<PrepOp>& ops, FusedPlan<V>& plan, bool fp_only, bool resident_ok, int kforce,
+                bool amp_ok) {
     plan.K = kforce > 0 ? kforce : fused_tile_bits(sizeof(V) == 16 ? MERA_C128 : MERA_C64, n);
     plan.n = n;
     const int L = low_bits_for(sizeof(V) == 16 ? MERA_C128 : MERA_C64, plan.K);
-    std::vector<Pass> passes = plan_passes(ops, n, plan.K, L);
     const size_t tile_bytes = ((size_t)1 << plan.K) * sizeof(V);
     MERA_RETURN_IF(tile_bytes > 227 * 1024, MERA_EUNSUPPORTED, "tile of %zu bytes exceeds shared memory", tile_bytes);
-    plan.args.assign(passes.size(), PassArgs<V>());
-    plan.eng.assign(passes.size(), 0);
-    plan.feat.assign(passes.size(), 0);
-    plan.single.assign(passes.size(), -1);
-    plan.hpass.assign(passes.size(), 0);
     plan.tabs.clear();
     // resident fixed point: complex128, unitary gates only (the norm bounds
     // every amplitude), some arithmetic to gain from it, and every mixing
@@ -1695,9 +2042,35 @@ int fused_build(int n, const std::vector<PrepOp>& ops, FusedPlan<V>& plan, bool 
         }
         plan.resident = unit && arith && !mixed_after;
     }
+    // affine monomial runs as single streaming passes: resident complex128
+    // plans with 12-bit tiles, out of place (MERA_AMP=0 turns them off)
+    bool amp_on = amp_ok && plan.resident && plan.K == 12 && n > 12 && n <= 40;
+    if (const char* e = getenv("MERA_AMP"))
+        if (atoi(e) == 0) amp_on = false;
+    std::vector<Pass> passes = plan_passes(ops, n, plan.K, L, amp_on);
+    plan.args.assign(passes.size(), PassArgs<V>());
+    plan.eng.assign(passes.size(), 0);
+    plan.feat.assign(passes.size(), 0);
+    plan.single.assign(passes.size(), -1);
+    plan.hpass.assign(passes.size(), 0);
+    plan.amp.assign(passes.size(), 0);
+    plan.aargs.assign(passes.size(), AmpArgs());
     for (size_t i = 0; i < passes.size(); ++i) {
         if (passes[i].single >= 0) {
             plan.single[i] = passes[i].single;
+            continue;
+        }
+        if (passes[i].amp) {
+            PassArgs<V>& A = plan.args[i];
+            memset(&A, 0, sizeof(A));
+            A.K = plan.K;
+            A.nph = 1;
+            A.qgi = 2;   // unit-modulus products: no growth
+            for (int b = 0; b < plan.K; ++b) A.tpos[b] = b;
+            plan.eng[i] = ENG_Q;
+            plan.amp[i] = 1;
+            MERA_TRY(amp_build<V>(ops, passes[i].ops, n, plan.tabs, plan.aargs[i]));
+            plan.qguard = std::max(plan.qguard, A.qgi);
             continue;
         }
         const size_t ntab0 = plan.tabs.size();
@@ -1803,6 +2176,12 @@ int fused_build(int n, const std::vector<PrepOp>& ops, FusedPlan<V>& plan, bool 
             A.q_in = (i > 0 && plan.single[i - 1] < 0) ? 1 : 0;
             A.q_out = (i + 1 < np && plan.single[i + 1] < 0) ? 1 : 0;
             A.qgo = A.q_out ? plan.args[i + 1].qgi : A.qgi;
+            if (plan.amp[i]) {
+                AmpArgs& g = plan.aargs[i];
+                g.qgi = A.qgi;
+                g.shift = A.q_out ? A.qgo - A.qgi : 0;
+                continue;
+            }
             // single phase of tables and sign terms between fixed-point
             // passes: the streaming kernel
             bool ok = A.nph == 1 && A.q_in && A.q_out && A.qend == 0 && !A.load_smem && !A.store_smem && plan.K == 12;
@@ -1828,7 +2207,7 @@ int fused_build(int n, const std::vector<PrepOp>& ops, FusedPlan<V>& plan, bool 
         };
         if (all_hp(plan)) {
             FusedPlan<V> wide;
-            if (fused_build<V>(n, ops, wide, fp_only, resident_ok, 13) == MERA_OK && all_hp(wide) &&
+            if (fused_build<V>(n, ops, wide, fp_only, resident_ok, 13, amp_ok) == MERA_OK && all_hp(wide) &&
                 wide.args.size() < plan.args.size())
                 plan = std::move(wide);
         }
@@ -1931,6 +2310,24 @@ int fused_launch(const FusedPlan<V>& plan, size_t i, PassArgs<V>& A, unsigned ny
     MERA_RETURN_IF(tiles > 0x7fffffffull, MERA_EUNSUPPORTED, "too many tiles");
     MERA_RETURN_IF(ny == 0 || ny > 65535, MERA_EUNSUPPORTED, "batch of %u states per launch", ny);
     const double pass_bytes = 2.0 * (double)(1ull << plan.n) * sizeof(V) * ny;
+    if (!plan.amp.empty() && plan.amp[i]) {
+        MERA_RETURN_IF(sizeof(V) != 16 || ny != 1, MERA_EUNSUPPORTED, "monomial run pass on a batch");
+        MERA_RETURN_IF(!A.psi_out || A.psi_out == A.psi, MERA_EUNSUPPORTED, "monomial run pass needs a second buffer");
+        AmpArgs g = plan.aargs[i];
+        g.psi = reinterpret_cast<const double2*>(A.psi);
+        g.psi_out = reinterpret_cast<double2*>(A.psi_out);
+        g.tab = reinterpret_cast<const int4*>(A.tab);
+        g.qS = A.qS;
+        MERA_RETURN_IF(!g.qS, MERA_EINVAL, "monomial run pass without the resident scale");
+        static int sms = 0;
+        if (!sms) MERA_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0));
+        const uint64_t ctas = std::max<uint64_t>(1, std::min<uint64_t>(g.ntiles, 16ull * (uint64_t)sms));
+        void* args[] = {&g};
+        launch_begin(st, MERA_KCLASS_AMP, pass_bytes);
+        MERA_CHECK_CUDA(cudaLaunchKernel(tile_fn_amp(A.q_in, A.q_out, plan.n > 32 ? 1 : 0), dim3((unsigned)ctas, 1),
+                                         dim3(512), args, 0, st));
+        return launch_end(st);
+    }
     if (sizeof(V) == 16 && ny == 1 && plan.dpass[i]) {
         DPassArgs d = plan.dargs[i];
         d.psi = reinterpret_cast<double2*>(A.psi);
@@ -2031,8 +2428,8 @@ int fused_launch(const FusedPlan<V>& plan, size_t i, PassArgs<V>& A, unsigned ny
     return launch_end(st);
 }
 
-template int fused_build<double2>(int, const std::vector<PrepOp>&, FusedPlan<double2>&, bool, bool, int);
-template int fused_build<float2>(int, const std::vector<PrepOp>&, FusedPlan<float2>&, bool, bool, int);
+template int fused_build<double2>(int, const std::vector<PrepOp>&, FusedPlan<double2>&, bool, bool, int, bool);
+template int fused_build<float2>(int, const std::vector<PrepOp>&, FusedPlan<float2>&, bool, bool, int, bool);
 template int fused_launch<double2>(const FusedPlan<double2>&, size_t, PassArgs<double2>&, unsigned, cudaStream_t);
 template int fused_launch<float2>(const FusedPlan<float2>&, size_t, PassArgs<float2>&, unsigned, cudaStream_t);
 
@@ -2078,6 +2475,41 @@ static int upload_plan(mera_state* s, FusedPlan<V>& plan) {
     return MERA_OK;
 }
 
+// The state's second buffer (allocated on first use); false once an
+// allocation failed (resident runs then go in place).
+static bool ensure_pong(mera_state* s) {
+    if (s->pong_failed) return false;
+    const size_t bytes = num_amps(s) * elem_bytes(s->dtype);
+    if (s->pong_bytes >= bytes) return true;
+    if (s->pong) {
+        if (cudaStreamSynchronize(s->stream) != cudaSuccess) return false;
+        cudaFree(s->pong);
+    }
+    s->pong = nullptr;
+    s->pong_bytes = 0;
+    if (cudaMalloc(&s->pong, bytes) == cudaSuccess) {
+        s->pong_bytes = bytes;
+        return true;
+    }
+    cudaGetLastError();
+    s->pong_failed = true;
+    return false;
+}
+
+// The plan of a circuit for this state: monomial run passes only when the
+// second buffer they write into is there.
+template <typename V>
+static int build_for_state(mera_state* s, const std::vector<PrepOp>& ops, FusedPlan<V>& plan) {
+    MERA_TRY(fused_build<V>(s->n, ops, plan, false, true, 0, !s->pong_failed));
+    bool any = false;
+    for (unsigned char a : plan.amp) any = any || a;
+    if (any && !ensure_pong(s)) {
+        plan = FusedPlan<V>();
+        MERA_TRY(fused_build<V>(s->n, ops, plan, false, true, 0, false));
+    }
+    return MERA_OK;
+}
+
 template <typename V>
 static int launch_plan(mera_state* s, FusedPlan<V>& plan, const std::vector<PrepOp>& ops) {
     if (plan.resident || plan.efmt) {
@@ -2091,24 +2523,7 @@ static int launch_plan(mera_state* s, FusedPlan<V>& plan, const std::vector<Prep
     // out of place need no load-before-store ordering); the buffers are
     // assigned so that every run ends in the state
     void* other = nullptr;
-    if (plan.resident && !s->pong_failed) {
-        const size_t bytes = num_amps(s) * elem_bytes(s->dtype);
-        if (s->pong_bytes < bytes) {
-            if (s->pong) {
-                MERA_CHECK_CUDA(cudaStreamSynchronize(s->stream));
-                cudaFree(s->pong);
-            }
-            s->pong = nullptr;
-            s->pong_bytes = 0;
-            if (cudaMalloc(&s->pong, bytes) == cudaSuccess) {
-                s->pong_bytes = bytes;
-            } else {
-                cudaGetLastError();
-                s->pong_failed = true;   // in place from now on
-            }
-        }
-        other = s->pong;
-    }
+    if (plan.resident && ensure_pong(s)) other = s->pong;
     const size_t np = plan.args.size();
     for (size_t i = 0; i < np;) {
         if (plan.single[i] >= 0) {
@@ -2119,16 +2534,28 @@ static int launch_plan(mera_state* s, FusedPlan<V>& plan, const std::vector<Prep
         size_t e = i;   // the run of tile passes [i, e)
         while (e < np && plan.single[e] < 0) ++e;
         V* bufs[2] = {reinterpret_cast<V*>(s->data), reinterpret_cast<V*>(other)};
+        // every pass writes the other buffer, except, in a run of odd
+        // length, its first pass that may run in place (monomial run passes
+        // may not); without one the run ends with a copy into the state
+        size_t stay = e;
+        if (other && (e - i) % 2 == 1)
+            for (size_t k = i; k < e; ++k)
+                if (!plan.amp[k]) {
+                    stay = k;
+                    break;
+                }
         int cur = 0;    // buffer holding the input
         for (size_t k = i; k < e; ++k) {
             PassArgs<V>& A = plan.args[k];
-            // pass k writes buffer (e - 1 - k) % 2 of {state, other}
-            const int dst = other ? (int)((e - 1 - k) % 2) : 0;
+            const int dst = !other ? 0 : (k == stay ? cur : cur ^ 1);
             A.psi = bufs[cur];
             A.psi_out = dst == cur ? nullptr : bufs[dst];
             MERA_TRY(fused_launch<V>(plan, k, A, 1, s->stream));
             cur = dst;
         }
+        if (cur != 0)
+            MERA_CHECK_CUDA(cudaMemcpyAsync(s->data, other, num_amps(s) * elem_bytes(s->dtype), cudaMemcpyDeviceToDevice,
+                                            s->stream));
         i = e;
     }
     // the wait status, read by the next synchronising call
@@ -2141,7 +2568,7 @@ template <typename V>
 static int run_fused(mera_state* s, const std::vector<PrepOp>& ops) {
     fused_cache_free(s);   // the program buffer is about to hold other tables
     FusedPlan<V> plan;
-    MERA_TRY(fused_build<V>(s->n, ops, plan, false, true));
+    MERA_TRY(build_for_state<V>(s, ops, plan));
     MERA_TRY(upload_plan<V>(s, plan));
     return launch_plan<V>(s, plan, ops);
 }
@@ -2188,7 +2615,7 @@ int apply_fused_circuit(mera_state* s, const mera_op* ops, size_t nops) {
     c->ops.swap(prep);
     int st;
     if (s->dtype == MERA_C128) {
-        st = fused_build<double2>(s->n, c->ops, c->p128, false, true);
+        st = build_for_state<double2>(s, c->ops, c->p128);
         if (st == MERA_OK) st = upload_plan<double2>(s, c->p128);
     } else {
         st = fused_build<float2>(s->n, c->ops, c->p64);
@@ -2208,7 +2635,7 @@ int apply_fused_circuit(mera_state* s, const mera_op* ops, size_t nops) {
 template <typename V>
 static int describe_fused(int n, int dtype, const std::vector<PrepOp>& ops, std::string* out, int* npasses) {
     FusedPlan<V> plan;
-    MERA_TRY(fused_build<V>(n, ops, plan, false, true));
+    MERA_TRY(fused_build<V>(n, ops, plan, false, true, 0, true));
     const int K = plan.K;
     char line[640];
     snprintf(line, sizeof(line), "K=%d L=%d passes=%zu resident=%d efmt=%d qguard=%d table_bytes=%zu\n", K,
@@ -2223,6 +2650,19 @@ static int describe_fused(int n, int dtype, const std::vector<PrepOp>& ops, std:
             continue;
         }
         const PassArgs<V>& A = plan.args[i];
+        if (plan.amp[i]) {
+            const AmpArgs& g = plan.aargs[i];
+            std::string bits;
+            for (int j = 0; j < K; ++j) bits += std::to_string(A.tpos[j]) + (j + 1 < K ? "," : "");
+            snprintf(line, sizeof(line),
+                     "pass %zu: eng=q feat=0 nh=0 phases=1 ops=%d [g1=0 mono=%d h=0 g2=0 diag=%d dsep=0 z4=0] guard=0 "
+                     "load_smem=0 store_smem=0 q_in=%d q_out=%d tile={%s} amp gather offsets=%d sel_a=%d tile_tab=%d "
+                     "z4_tile=%d z4_elem=%d qend=0 qexit=0 qgi=%d phase_ops=[%d]\n",
+                     i, g.nperm + g.ndiag, g.nperm, g.ndiag, A.q_in, A.q_out, bits.c_str(), g.in_nq, g.a_nt,
+                     g.t_off >= 0 ? g.t_nt : 0, g.ntz, g.nz, A.qgi, g.nperm + g.ndiag);
+            *out += line;
+            continue;
+        }
         const int nop = A.nph > 0 ? A.ph[A.nph - 1].op_end : 0;
         int cnt[16] = {0};
         for (int o = 0; o < nop; ++o) cnt[A.ops[o].type]++;

@@ -19,6 +19,8 @@ struct FusedPlan {
     std::vector<unsigned char> dpass;     // 1: single-phase table pass for the streaming kernel
     std::vector<DPassArgs> dargs;         // its arguments (state / table pointers set at launch)
     std::vector<unsigned char> hpass;     // 1: Hadamard / sign-term pass for the pipelined kernel
+    std::vector<unsigned char> amp;       // 1: affine monomial run (k_amp, out of place)
+    std::vector<AmpArgs> aargs;           // its arguments (state / table pointers set at launch)
     bool resident = false;                // complex128 state kept as int64 fixed point (ENG_Q)
     int qguard = 0;                       // ENG_Q: headroom bits above the state norm
     bool efmt = false;                    // ENG_I64 Hadamard runs keep per-amplitude exponents between passes
@@ -27,6 +29,8 @@ struct FusedPlan {
 };
 
 // fp_only: every pass in the float engine (coefficients as plain values).
+// amp_ok: runs of affine monomial gates of a resident plan may become single
+// out-of-place passes (the caller provides a second state-sized buffer).
 // resident_ok: a complex128 circuit of unitary gates whose mixing gates all
 // precede a monomial body may keep the state in int64 fixed point across
 // its passes, and runs of Hadamard passes of any unitary circuit may keep
@@ -35,7 +39,7 @@ struct FusedPlan {
 // fixes the tile bits.
 template <typename V>
 int fused_build(int n, const std::vector<PrepOp>& ops, FusedPlan<V>& plan, bool fp_only = false,
-                bool resident_ok = false, int kforce = 0);
+                bool resident_ok = false, int kforce = 0, bool amp_ok = false);
 // S = 59 - floor(log2 of a bound of the norm of the complex128 state psi
 // (2^n amplitudes)); a pass with g headroom bits stores value * 2^(S - g).
 // Uses 16 KiB of scratch; S is written to scratch + 8192.

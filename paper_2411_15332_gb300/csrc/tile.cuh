@@ -1077,18 +1077,23 @@ __device__ __forceinline__ long long shr_lt32(long long v, int k) {
     const int nhi = (int)hi >> k;
     return (long long)(((unsigned long long)(unsigned)nhi << 32) | nlo);
 }
+// (hi:lo) << k for 0 <= k < 32: a funnel shift and a shift
+__device__ __forceinline__ long long shl_lt32(long long v, int k) {
+    const unsigned lo = (unsigned)v, hi = (unsigned)(v >> 32);
+    return (long long)(((unsigned long long)__funnelshift_l(lo, hi, k) << 32) | (lo << k));
+}
 // Per-amplitude exponent format of the int64 engine between Hadamard passes
-// (EF).  A complex128 amplitude is two int64 words: bits 6..63 of each hold
-// a signed mantissa (re, im), bits 0..5 of the real word the amplitude's
-// exponent code e (0..63), bits 0..5 of the imaginary word are 0; value =
-// mantissa * 2^-(e + B), B a bias fixed per circuit from the state's norm
-// bound.  A stored amplitude has max(|re|, |im|) in [2^52, 2^53] (53
-// significant bits, as in a double) unless it is below the normal range,
-// where e = 63 keeps it unnormalised (zero included).  The mantissa sits
-// where a pass with 9 headroom bits wants the tile's largest amplitude, so
-// most amplitudes load with a shift by a few bits to the left (exact) and
-// only those below the tile's largest exponent round.
-constexpr int EF_LZ = 11;         // leading zeros of a normalised mantissa word before the shift by 6
+// (EF).  A complex128 amplitude is two int64 words: bits 6..63 of the real
+// word hold its signed real mantissa and bits 0..5 the amplitude's
+// exponent code e (0..63); the imaginary word is the signed imaginary
+// mantissa; value = mantissa * 2^-(e + B), B a bias fixed per circuit from
+// the state's norm bound.  A stored amplitude has max(|re|, |im|) in
+// [2^52, 2^53] (53 significant bits, as in a double) unless it is below
+// the normal range, where e = 63 keeps it unnormalised (zero included).
+// The mantissa sits where a pass with 9 headroom bits wants the tile's
+// largest amplitude, so most amplitudes load with a shift by a few bits to
+// the left (exact) and only those below the tile's largest exponent round.
+constexpr int EF_LZ = 11;         // leading zeros of a normalised mantissa (top bit at 52)
 constexpr int EF_TOP = 53;        // |mantissa| <= 2^EF_TOP
 
 // round(v / 2^s), s >= 1 (0 for s >= 63)
@@ -1096,37 +1101,121 @@ __device__ __forceinline__ long long ef_rshift(long long v, int s) {
     if (s >= 63) return 0;
     return (v + (1ll << (s - 1))) >> s;
 }
+// v * 2^-s rounded to nearest (ties up) for -32 < s < 32
+__device__ __forceinline__ long long shift_round_lt32(long long v, int s) {
+    if (s <= 0) return shl_lt32(v, -s);
+    return shr_lt32(v + (long long)(1u << (s - 1)), s);
+}
 // amplitude (vx, vy) = value * 2^T into the two EF words
 __device__ __forceinline__ double2 ef_store(long long vx, long long vy, int T, int B) {
-    const unsigned long long a = (unsigned long long)((vx < 0 ? -vx : vx) | (vy < 0 ? -vy : vy));
-    if (a == 0) return make_double2(__longlong_as_double(63ll), 0.0);
-    int sl = __clzll((long long)a) - EF_LZ;     // shift that puts the top bit at 52
+    if ((vx | vy) == 0) return make_double2(__longlong_as_double(63ll), 0.0);
+    // ones' complement magnitudes: |v| - 1 for v < 0, which moves the top
+    // bit only for powers of two, whose shifted mantissa is then 2^53
+    const unsigned long long a = (unsigned long long)((vx ^ (vx >> 63)) | (vy ^ (vy >> 63)));
+    int sl = __clzll((long long)a) - EF_LZ;     // shift that puts the top bit at 52 (a = 0: v in {0, -1})
     int e = T + sl - B;
     if (e > 63) {                               // below the normal range
         sl -= e - 63;
         e = 63;
     }
-    const long long mx = sl >= 0 ? (long long)((unsigned long long)vx << sl) : ef_rshift(vx, -sl);
-    const long long my = sl >= 0 ? (long long)((unsigned long long)vy << sl) : ef_rshift(vy, -sl);
+    long long mx, my;
+    if (sl > -32 && sl < 32) {
+        mx = shift_round_lt32(vx, -sl);
+        my = shift_round_lt32(vy, -sl);
+    } else {
+        mx = sl >= 0 ? (long long)((unsigned long long)vx << sl) : ef_rshift(vx, -sl);
+        my = sl >= 0 ? (long long)((unsigned long long)vy << sl) : ef_rshift(vy, -sl);
+    }
     return make_double2(__longlong_as_double((long long)(((unsigned long long)mx << 6) | (unsigned)e)),
-                        __longlong_as_double((long long)((unsigned long long)my << 6)));
+                        __longlong_as_double(my));
 }
 
-// Butterflies on the register bits set in m: a full phase (all four bits)
-// as one straight block, otherwise bit by bit.
-template <typename V>
-__device__ __forceinline__ void op_hmask(V (&x)[FRA], int m) {
-    if (m == 15) {
-        op_h<V, 0>(x);
-        op_h<V, 1>(x);
-        op_h<V, 2>(x);
-        op_h<V, 3>(x);
-        return;
+// Integer butterflies on register bit B that also add h to every result
+// (the rounding term of a shift that follows): a + b + h, a - b + h.
+template <int B>
+__device__ __forceinline__ void op_h_add(I2 (&x)[FRA], long long h) {
+#pragma unroll
+    for (int j = 0; j < FRA; ++j) {
+        if (j & (1 << B)) continue;
+        const int j1 = j | (1 << B);
+        x[j].x += x[j1].x + h;
+        x[j].y += x[j1].y + h;
+        x[j1].x = x[j].x - x[j1].x - x[j1].x;
+        x[j1].y = x[j].y - x[j1].y - x[j1].y;
     }
-    if (m & 1) op_h<V, 0>(x);
-    if (m & 2) op_h<V, 1>(x);
-    if (m & 4) op_h<V, 2>(x);
-    if (m & 8) op_h<V, 3>(x);
+}
+// Integer butterflies on register bits B0 and B0 + 1 at once (two levels):
+// for a, b, c, d on slots j, j|1<<B0, j|2<<B0, j|3<<B0 the results
+// a+b+c+d, a-b+c-d, a+b-c-d, a-b-c+d from S = c + d and D = c - d in six
+// three-operand sums instead of eight two-operand ones.
+template <int B0>
+__device__ __forceinline__ void op_h4(I2 (&x)[FRA]) {
+#pragma unroll
+    for (int j = 0; j < FRA; ++j) {
+        if (j & (3 << B0)) continue;
+        const int j1 = j | (1 << B0), j2 = j | (2 << B0), j3 = j | (3 << B0);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            long long& a = c ? x[j].y : x[j].x;
+            long long& b = c ? x[j1].y : x[j1].x;
+            long long& cc = c ? x[j2].y : x[j2].x;
+            long long& d = c ? x[j3].y : x[j3].x;
+            const long long S = cc + d, D = S - d - d;
+            const long long y0 = a + b + S, y1 = a - b + D;
+            a = y0;
+            b = y1;
+            cc = y0 - S - S;
+            d = y1 - D - D;
+        }
+    }
+}
+// Butterflies on the register bits set in m: a full phase (all four bits)
+// as one straight block, otherwise bit by bit.  Integer engines: pairs of
+// levels as radix-4 blocks; h != 0 adds h to every result of the last
+// level (the rounding term of the phase's exit shift).
+template <typename V>
+__device__ __forceinline__ void op_hmask(V (&x)[FRA], int m, long long h = 0) {
+    if constexpr (IsFP<V>::value) {
+        if (m == 15) {
+            op_h<V, 0>(x);
+            op_h<V, 1>(x);
+            op_h<V, 2>(x);
+            op_h<V, 3>(x);
+            return;
+        }
+        if (m & 1) op_h<V, 0>(x);
+        if (m & 2) op_h<V, 1>(x);
+        if (m & 4) op_h<V, 2>(x);
+        if (m & 8) op_h<V, 3>(x);
+    } else {
+        if (m == 15) {
+            op_h4<0>(x);
+            if (h != 0) {
+                op_h<V, 2>(x);
+                op_h_add<3>(x, h);
+            } else {
+                op_h4<2>(x);
+            }
+            return;
+        }
+        const int top = 31 - __clz(m | 1);   // the last level applied
+        if (m & 1) {
+            if (h != 0 && top == 0) op_h_add<0>(x, h);
+            else op_h<V, 0>(x);
+        }
+        if (m & 2) {
+            if (h != 0 && top == 1) op_h_add<1>(x, h);
+            else op_h<V, 1>(x);
+        }
+        if (m & 4) {
+            if (h != 0 && top == 2) op_h_add<2>(x, h);
+            else op_h<V, 2>(x);
+        }
+        if (m & 8) {
+            if (h != 0 && top == 3) op_h_add<3>(x, h);
+            else op_h<V, 3>(x);
+        }
+    }
 }
 
 // QIN: 1 = the pass converts its input from doubles, 0 = it reads the
@@ -1303,13 +1392,13 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
 #pragma unroll
                     for (int j = 0; j < FRA; ++j) {
                         const int sh = (int)(x[j].x & 63) + sh0;
-                        const long long mx = x[j].x >> 6, my = x[j].y >> 6;
-                        if (sh > 0) {
+                        const long long mx = x[j].x >> 6, my = x[j].y;
+                        if (sh < 32) {   // sh > -32: codes are >= emin, guard >= 0
+                            x[j].x = shift_round_lt32(mx, sh);
+                            x[j].y = shift_round_lt32(my, sh);
+                        } else {
                             x[j].x = ef_rshift(mx, sh);
                             x[j].y = ef_rshift(my, sh);
-                        } else {
-                            x[j].x = (long long)((unsigned long long)mx << (-sh));
-                            x[j].y = (long long)((unsigned long long)my << (-sh));
                         }
                     }
                 }
@@ -1322,12 +1411,17 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
                 __syncthreads();
                 prefetch(tile + G, tbn);
             }
+            bool rounded = false;   // the exit's rounding term was added by the last butterflies
             for (int o = ph.op_begin; o < ph.op_end;) {
                 const TileOp& op = a.ops[o];
                 if (op.type == TOP_H) {
                     const int r = h.hrun[o];
-                    op_hmask<V>(x, r & 15);
                     o += max(r >> 4, 1);   // (a run covers at least this op)
+                    // a run that ends a phase with a rounded exit shift adds
+                    // the rounding term in its last level
+                    const bool fuse = o >= ph.op_end && p != a.nph - 1 && ph.qsh > 0;
+                    op_hmask<V>(x, r & 15, fuse ? (1ll << (ph.qsh - 1)) : 0ll);
+                    rounded = rounded || fuse;
                     continue;
                 }
                 ++o;
@@ -1386,7 +1480,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
                 // shift rounded to nearest (ties up), both engines
                 if (ph.qsh > 0) {
                     const int k = ph.qsh;
-                    const long long half = 1ll << (k - 1);
+                    const long long half = rounded ? 0ll : (1ll << (k - 1));
 #pragma unroll
                     for (int j = 0; j < FRA; ++j) {
                         x[j].x = shr_lt32(x[j].x + half, k);
@@ -1636,6 +1730,134 @@ __global__ void __launch_bounds__(512, 2) k_dpass(const __grid_constant__ DPassA
         }
     }
     }   // tiles (disjoint index sets: no ordering between them is needed)
+}
+
+// ------------------------------------------------- affine monomial run --
+// One pass for a run of monomial gates whose index maps are affine over
+// GF(2) (X, CNOT, SWAP, any permutation of two or three qubits) followed by
+// diagonal gates: the run's product is one monomial operator (a DAX: one
+// nonzero per row), out[i] = D(i) in[F^-1(i)], with F the composed affine
+// index map and D the product of the diagonals on the output index.  The
+// output is walked in tiles of its 12 low bits (thread bits 0..8, register
+// bits 9..11: every store is a coalesced row); each amplitude is gathered
+// from F^-1(i), whose 128-byte rows the low bits keep together.  D is two
+// table lookups: table A over the 12 local bits and up to 8 selected tile
+// bits, and a per-tile factor from table T over the remaining tile bits
+// (with exact sign terms on tile bits); sign terms with local bits outside
+// A's selection apply per amplitude.  Out of place only (tiles read other
+// tiles' amplitudes).  Resident int64 fixed point, as the table pass; QIN /
+// QOUT = 0 convert from / to doubles at the run's ends.
+constexpr int AMP_MAX_XOFF = 48;
+constexpr int AMP_MAX_Z4 = 16;
+constexpr int AMP_MAX_TZ4 = 32;
+constexpr int AMP_A_SEL = 8;
+constexpr int AMP_T_BITS = 16;
+struct AmpArgs {
+    const double2* psi;
+    double2* psi_out;              // must differ from psi
+    const int4* tab;
+    const int* qS;                 // resident scale exponent (device)
+    unsigned long long in_t[DPASS_TBITS], in_r[DPASS_RBITS], in_c;   // F^-1 of thread / register bits, of 0
+    unsigned long long in_w[AMP_MAX_XOFF];   // F^-1(e_q) ^ e_q for tile bit q = in_q[i]
+    int8_t in_q[AMP_MAX_XOFF];
+    int in_nq;
+    int a_off, a_nt;               // table A: 2^(12 + a_nt) entries at tab + a_off
+    int8_t a_q[AMP_A_SEL];
+    int t_off, t_nt;               // table T: 2^t_nt entries (t_off < 0: none)
+    int8_t t_q[AMP_T_BITS];
+    int ntz;                       // sign terms on tile bits (per tile)
+    DZ4 tz[AMP_MAX_TZ4];
+    int nz;                        // sign terms with local bits (per amplitude, output index)
+    DZ4 z4[AMP_MAX_Z4];
+    int qgi;                       // input format: value * 2^(*qS - qgi)
+    int shift;                     // right shift into the next pass's format
+    uint32_t ntiles;
+    int nperm, ndiag;              // the run's gates (description only)
+};
+
+__device__ __forceinline__ uint32_t amp_sel(unsigned long long v, const int8_t* q, int nt) {
+    uint32_t s = 0;
+    for (int f = 0; f < nt; ++f) s |= (uint32_t)((v >> q[f]) & 1ull) << f;
+    return s;
+}
+__device__ __forceinline__ int4 q61_split(long long re, long long im) {
+    return make_int4((int)(re >> 31), (int)((unsigned)re & 0x7FFFFFFFu), (int)(im >> 31),
+                     (int)((unsigned)im & 0x7FFFFFFFu));
+}
+
+template <int QIN, int QOUT, typename IX>
+__global__ void __launch_bounds__(512, 2) k_amp(const __grid_constant__ AmpArgs a) {
+    constexpr int NA = 1 << DPASS_RBITS;
+    const uint32_t tid = threadIdx.x;
+    IX ti = (IX)a.in_c;
+#pragma unroll
+    for (int t = 0; t < DPASS_TBITS; ++t) ti ^= ((IX)0 - (IX)((tid >> t) & 1u)) & (IX)a.in_t[t];
+    IX rin[DPASS_RBITS];
+#pragma unroll
+    for (int r = 0; r < DPASS_RBITS; ++r) rin[r] = (IX)a.in_r[r];
+    const int S = *a.qS - a.qgi;
+    for (uint32_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+        const IX tb = (IX)tile << 12;
+        IX gi0 = tb ^ ti;
+        for (int i = 0; i < a.in_nq; ++i)
+            if ((tb >> a.in_q[i]) & 1u) gi0 ^= (IX)a.in_w[i];
+        const IX go0 = tb | (IX)tid;
+        const int4* A = a.tab + a.a_off + ((size_t)amp_sel(tb, a.a_q, a.a_nt) << 12);
+        // per-tile factor: table T and the sign terms on tile bits
+        int et = 0;
+        for (int z = 0; z < a.ntz; ++z)
+            if ((tb & (IX)a.tz[z].mask) == (IX)a.tz[z].vals) et += a.tz[z].e;
+        const bool tf = a.t_off >= 0 || (et & 3) != 0;
+        int4 f = make_int4(1 << 30, 0, 0, 0);   // 1 in split Q61
+        if (a.t_off >= 0) f = __ldg(a.tab + a.t_off + amp_sel(tb, a.t_q, a.t_nt));
+        if (et & 3) {
+            I2 v;
+            v.x = ((long long)f.x << 31) + (long long)(unsigned)f.y;
+            v.y = ((long long)f.z << 31) + (long long)(unsigned)f.w;
+            v = mul_ik(v, et & 3);
+            f = q61_split(v.x, v.y);
+        }
+        I2 x[NA];
+#pragma unroll
+        for (int j = 0; j < NA; ++j) {
+            const longlong2 v = __ldcs(reinterpret_cast<const longlong2*>(a.psi + (gi0 ^ dreg<IX>(j, rin))));
+            if constexpr (QIN == 0) {
+                x[j].x = d2fix(__longlong_as_double(v.x), S);
+                x[j].y = d2fix(__longlong_as_double(v.y), S);
+            } else {
+                x[j].x = v.x;
+                x[j].y = v.y;
+            }
+        }
+        const int k = a.shift;
+        const long long half = k > 0 ? (1ll << (k - 1)) : 0ll;
+#pragma unroll
+        for (int j = 0; j < NA; ++j) {
+            const uint32_t l = tid | ((uint32_t)j << 9);
+            x[j] = qcmul(__ldg(A + l), x[j]);
+            if (tf) x[j] = qcmul(f, x[j]);
+            if (a.nz) {
+                const IX go = go0 | ((IX)j << 9);
+                int e = 0;
+                for (int z = 0; z < a.nz; ++z)
+                    if ((go & (IX)a.z4[z].mask) == (IX)a.z4[z].vals) e += a.z4[z].e;
+                x[j] = mul_ik(x[j], e & 3);
+            }
+            long long vx = x[j].x, vy = x[j].y;
+            if constexpr (QOUT == 0) {
+                __stcs(a.psi_out + (go0 | ((IX)j << 9)), make_double2(fix2d(vx, S), fix2d(vy, S)));
+            } else {
+                if (k > 0) {
+                    vx = (vx + half) >> k;
+                    vy = (vy + half) >> k;
+                } else if (k < 0) {
+                    vx = (long long)((unsigned long long)vx << (-k));
+                    vy = (long long)((unsigned long long)vy << (-k));
+                }
+                __stcs(reinterpret_cast<longlong2*>(a.psi_out + (go0 | ((IX)j << 9))), make_longlong2(vx, vy));
+            }
+        }
+    }
 }
 
 }  // namespace mera

@@ -13,6 +13,8 @@ const void* tile_fn_q(int feat, int qin);
 // the streaming kernel of single-phase table passes (resident engine);
 // wide = 1: 64-bit indices (states of more than 2^32 amplitudes)
 const void* tile_fn_dpass(int wide);
+// affine monomial run pass: qin / qout = 1 for the resident format (0: doubles)
+const void* tile_fn_amp(int qin, int qout, int wide);
 const void* tile_fn_i64(int feat, int qin);
 // the Hadamard-pass kernel (ENG_I64 or ENG_Q): qin = 1 when the pass reads
 // doubles, qout = 1 when it writes the engine's own format (ENG_Q: global

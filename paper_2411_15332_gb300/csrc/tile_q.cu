@@ -8,6 +8,15 @@ const void* tile_fn_dpass(int wide) {
     return wide ? (const void*)k_dpass<4, unsigned long long> : (const void*)k_dpass<4, uint32_t>;
 }
 
+template <typename IX>
+static const void* amp_fn(int qin, int qout) {
+    if (qin) return qout ? (const void*)k_amp<1, 1, IX> : (const void*)k_amp<1, 0, IX>;
+    return qout ? (const void*)k_amp<0, 1, IX> : (const void*)k_amp<0, 0, IX>;
+}
+const void* tile_fn_amp(int qin, int qout, int wide) {
+    return wide ? amp_fn<unsigned long long>(qin, qout) : amp_fn<uint32_t>(qin, qout);
+}
+
 const void* tile_fn_q(int feat, int qin) {
     if (qin) {
         switch (feat) {

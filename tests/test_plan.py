@@ -35,16 +35,36 @@ def parse(summary):
 
 
 def test_layered_n30_plan(core):
-    head, passes = parse(core.plan_summary(30, inputs.layered_circuit(30, 20, seed=2)))
-    assert head["resident"] == 1 and head["passes"] == 60
+    """Three Hadamard passes, then one pass per layer: each layer (CNOT
+    ladder, CZ matching, T/S, RZ on all) is one monomial operator applied
+    by a single streaming pass."""
+    summary = core.plan_summary(30, inputs.layered_circuit(30, 20, seed=2))
+    head, passes = parse(summary)
+    lines = summary.splitlines()[1:]
+    assert head["resident"] == 1 and head["passes"] == 23
     assert all(p["eng"] == "q" for p in passes)
-    # the CNOT ladders ride on the exchanges: no register permutation op
-    assert all(p["mono"] == "0" for p in passes)
-    # at most one separable-diagonal table per pass
-    assert all(int(p["dsep"]) <= 2 for p in passes)
+    assert all("pipelined" in l for l in lines[:3])
+    amp = [l for l in lines if " amp " in l]
+    assert len(amp) == 20 and all("ops=89 " in l and "mono=29 " in l and "diag=60 " in l for l in amp)
     # the resident run converts from doubles once and back once
     assert passes[0]["q_in"] == "0" and passes[-1]["q_out"] == "0"
     assert all(p["q_in"] == "1" for p in passes[1:]) and all(p["q_out"] == "1" for p in passes[:-1])
+
+
+def test_layered_n30_plan_without_monomial_runs(core):
+    """The tile planner alone (MERA_AMP=0 is read per plan): three passes per
+    layer, the CNOT ladders riding on exchanges."""
+    import subprocess
+    import sys
+    code = ("from paper_2411_15332_gb300 import core, inputs\n"
+            "print(core.plan_summary(30, inputs.layered_circuit(30, 20, seed=2)))\n")
+    out = subprocess.run([sys.executable, "-c", code], env={**__import__("os").environ, "MERA_AMP": "0"},
+                         capture_output=True, text=True, check=True, timeout=300).stdout.strip()
+    head, passes = parse(out)
+    assert head["resident"] == 1 and head["passes"] == 60
+    assert " amp " not in out
+    assert all(p["mono"] == "0" for p in passes)
+    assert all(int(p["dsep"]) <= 2 for p in passes)
 
 
 def test_hadamard_levels_per_pass_are_capped(core):
@@ -210,11 +230,11 @@ def test_hadamard_kernel_eligibility(core):
         if has_table:
             assert "pipelined" not in line
     assert any("pipelined" in l for l in lines)
-    # the layered circuit: its three Hadamard passes carry the CNOT run after
-    # them on scattered stores and still run in the kernel
+    # the layered circuit: its three Hadamard passes run in the kernel (the
+    # CNOT ladder after them starts the first monomial run pass)
     summary = core.plan_summary(30, inputs.layered_circuit(30, 20, seed=2)).splitlines()[1:]
     hp = [l for l in summary if "pipelined" in l]
-    assert len(hp) == 3 and all("scatter" in l and "gather" not in l for l in hp)
+    assert len(hp) == 3 and all("gather" not in l for l in hp)
 
 
 def test_bulk_staging_eligibility(core):
