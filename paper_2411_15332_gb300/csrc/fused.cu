@@ -1932,7 +1932,6 @@ static int amp_build(const std::vector<PrepOp>& ops, const std::vector<int>& run
             }
             tabs[a.t_off + v] = PassBuilder<V>::enc_split(d);
         }
-        (void)sel_of;
     }
     for (int ti : L.tileZ) {
         const AmpTerm& t = r.terms[ti];
@@ -1943,12 +1942,69 @@ static int amp_build(const std::vector<PrepOp>& ops, const std::vector<int>& run
     }
     for (int ti : L.elemZ) {
         const AmpTerm& t = r.terms[ti];
-        a.z4[a.nz].mask = t.mask;
-        a.z4[a.nz].vals = t.vals;
+        const uint64_t RB = 7ull << DPASS_TBITS;   // register bits 9..11
+        a.z4[a.nz].mask = t.mask & ~RB;
+        a.z4[a.nz].vals = t.vals & ~RB;
         a.z4[a.nz].e = (int16_t)unit_exp(t.v);
+        uint8_t J = 0;
+        for (int j = 0; j < (1 << DPASS_RBITS); ++j)
+            if ((((uint64_t)j << DPASS_TBITS) & t.mask) == (t.vals & RB)) J |= (uint8_t)(1u << j);
+        a.z4j[a.nz] = J;
         ++a.nz;
     }
     a.ntiles = (uint32_t)(1ull << (n - 12));
+    // tile groups: H = span of the tile parts of F(e_0), F(e_1), F(e_2) in
+    // echelon form (distinct pivot bits); groups enumerate the other bits
+    const int nt = n - 12;
+    uint32_t hb[3];
+    int h = 0, piv[3];
+    for (int k = 0; k < 3; ++k) {
+        uint32_t v = (uint32_t)(r.col[k] >> 12);
+        for (int u = 0; u < h; ++u)
+            if ((v >> piv[u]) & 1u) v ^= hb[u];
+        if (!v) continue;
+        const int p = 31 - __builtin_clz(v);
+        for (int u = 0; u < h; ++u)
+            if ((hb[u] >> p) & 1u) hb[u] ^= v;
+        hb[h] = v;
+        piv[h++] = p;
+    }
+    a.h = h;
+    for (int u = 0; u < (1 << h); ++u) {
+        uint32_t v = 0;
+        for (int b = 0; b < h; ++b)
+            if ((u >> b) & 1) v ^= hb[b];
+        a.hv[u] = v;
+        a.dgi[u] = minv((uint64_t)v << 12);
+        a.dasel[u] = sel_of((uint64_t)v << 12, sq, ns);
+        uint32_t ts = 0;
+        for (int f = 0; f < a.t_nt; ++f) ts |= (uint32_t)(((uint64_t)v << 12 >> a.t_q[f]) & 1ull) << f;
+        a.dtsel[u] = ts;
+    }
+    a.ngroups = (uint32_t)(1ull << (nt - h));
+    int src = 0;
+    for (int b = 0; b < nt;) {
+        bool pv = false;
+        for (int u = 0; u < h; ++u) pv = pv || piv[u] == b;
+        if (pv) {
+            ++b;
+            continue;
+        }
+        int w = 1;
+        auto isp = [&](int q) {
+            for (int u = 0; u < h; ++u)
+                if (piv[u] == q) return true;
+            return false;
+        };
+        while (b + w < nt && !isp(b + w)) ++w;
+        MERA_RETURN_IF(a.g_nruns >= 8, MERA_EUNSUPPORTED, "tile group runs");
+        a.g_src[a.g_nruns] = (uint32_t)src;
+        a.g_w[a.g_nruns] = (uint32_t)w;
+        a.g_dst[a.g_nruns] = (uint32_t)b;
+        ++a.g_nruns;
+        src += w;
+        b += w;
+    }
     for (int idx : run_ops) (ops[idx].kind == KIND_MONO ? a.nperm : a.ndiag) += 1;
     return MERA_OK;
 }
@@ -2321,7 +2377,7 @@ int fused_launch(const FusedPlan<V>& plan, size_t i, PassArgs<V>& A, unsigned ny
         MERA_RETURN_IF(!g.qS, MERA_EINVAL, "monomial run pass without the resident scale");
         static int sms = 0;
         if (!sms) MERA_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0));
-        const uint64_t ctas = std::max<uint64_t>(1, std::min<uint64_t>(g.ntiles, 16ull * (uint64_t)sms));
+        const uint64_t ctas = std::max<uint64_t>(1, std::min<uint64_t>(g.ngroups, 16ull * (uint64_t)sms));
         void* args[] = {&g};
         launch_begin(st, MERA_KCLASS_AMP, pass_bytes);
         MERA_CHECK_CUDA(cudaLaunchKernel(tile_fn_amp(A.q_in, A.q_out, plan.n > 32 ? 1 : 0), dim3((unsigned)ctas, 1),
@@ -2657,9 +2713,9 @@ static int describe_fused(int n, int dtype, const std::vector<PrepOp>& ops, std:
             snprintf(line, sizeof(line),
                      "pass %zu: eng=q feat=0 nh=0 phases=1 ops=%d [g1=0 mono=%d h=0 g2=0 diag=%d dsep=0 z4=0] guard=0 "
                      "load_smem=0 store_smem=0 q_in=%d q_out=%d tile={%s} amp gather offsets=%d sel_a=%d tile_tab=%d "
-                     "z4_tile=%d z4_elem=%d qend=0 qexit=0 qgi=%d phase_ops=[%d]\n",
+                     "z4_tile=%d z4_elem=%d group=%d qend=0 qexit=0 qgi=%d phase_ops=[%d]\n",
                      i, g.nperm + g.ndiag, g.nperm, g.ndiag, A.q_in, A.q_out, bits.c_str(), g.in_nq, g.a_nt,
-                     g.t_off >= 0 ? g.t_nt : 0, g.ntz, g.nz, A.qgi, g.nperm + g.ndiag);
+                     g.t_off >= 0 ? g.t_nt : 0, g.ntz, g.nz, 1 << g.h, A.qgi, g.nperm + g.ndiag);
             *out += line;
             continue;
         }

@@ -142,6 +142,28 @@ __device__ __forceinline__ I2 qcmul(int4 d, I2 x) {
     r.y = k1 + k2;
     return r;
 }
+// qcmul without the low-by-low limb products: each real product takes
+// the mean of that term over uniform low limbs (2^29 at the scale of the
+// middle terms) instead: error within two units per real product, its
+// mean within half a unit of zero; one high product and three adds fewer
+// per real product.
+__device__ __forceinline__ long long qmul_q_fast(long long x, int ch, int cl) {
+    int h, l;
+    qsplit(x, h, l);
+    return 2 * ((long long)h * ch) + (((long long)h * cl + (long long)l * ch + (1ll << 30)) >> 30);
+}
+__device__ __forceinline__ I2 qcmul_fast(int4 d, I2 x) {
+    const long long c = ((long long)d.x << 31) + (long long)(unsigned)d.y;
+    const long long e = ((long long)d.z << 31) + (long long)(unsigned)d.w;
+    const long long dmc = e - c, cpd = c + e;
+    const long long k1 = qmul_q_fast(x.x + x.y, d.x, d.y);
+    const long long k2 = qmul_q_fast(x.x, (int)(dmc >> 31), (int)((unsigned)dmc & 0x7FFFFFFFu));
+    const long long k3 = qmul_q_fast(x.y, (int)(cpd >> 31), (int)((unsigned)cpd & 0x7FFFFFFFu));
+    I2 r;
+    r.x = k1 - k3;
+    r.y = k1 + k2;
+    return r;
+}
 __device__ __forceinline__ long long sneg(long long v) { return -v; }
 __device__ __forceinline__ I2 neg_v(I2 x) {
     x.x = -x.x;

@@ -1767,11 +1767,24 @@ struct AmpArgs {
     int8_t t_q[AMP_T_BITS];
     int ntz;                       // sign terms on tile bits (per tile)
     DZ4 tz[AMP_MAX_TZ4];
-    int nz;                        // sign terms with local bits (per amplitude, output index)
-    DZ4 z4[AMP_MAX_Z4];
+    int nz;                        // sign terms with local bits: match on the output index outside
+    DZ4 z4[AMP_MAX_Z4];            // register bits 9..11 (mask, vals), e = i^e ...
+    uint8_t z4j[AMP_MAX_Z4];       // ... on the registers j whose bits 9..11 match (bit j)
     int qgi;                       // input format: value * 2^(*qS - qgi)
     int shift;                     // right shift into the next pass's format
     uint32_t ntiles;
+    // Tile groups: the output tiles whose amplitudes come from the same
+    // input rows (the images of row bits 0..2 under F, above bit 11) run
+    // one after another in one CTA, so that a row read in halves is read
+    // from DRAM once.  Tile (g, u) = base(g) ^ hv[u], base(g) deposits g
+    // into the tile-index bits outside the group's pivots (runs).
+    uint32_t ngroups;
+    int h;                         // 2^h tiles per group (h <= 3)
+    uint32_t hv[8];
+    unsigned long long dgi[8];     // F^-1(hv[u] << 12)
+    uint32_t dasel[8], dtsel[8];   // selection bits of hv[u] << 12 for tables A and T
+    int g_nruns;
+    uint32_t g_src[8], g_w[8], g_dst[8];
     int nperm, ndiag;              // the run's gates (description only)
 };
 
@@ -1796,20 +1809,27 @@ __global__ void __launch_bounds__(512, 2) k_amp(const __grid_constant__ AmpArgs 
 #pragma unroll
     for (int r = 0; r < DPASS_RBITS; ++r) rin[r] = (IX)a.in_r[r];
     const int S = *a.qS - a.qgi;
-    for (uint32_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-        const IX tb = (IX)tile << 12;
-        IX gi0 = tb ^ ti;
-        for (int i = 0; i < a.in_nq; ++i)
-            if ((tb >> a.in_q[i]) & 1u) gi0 ^= (IX)a.in_w[i];
+    for (uint32_t grp = blockIdx.x; grp < a.ngroups; grp += gridDim.x) {
+    uint32_t base = 0;
+    for (int i = 0; i < a.g_nruns; ++i) base |= ((grp >> a.g_src[i]) & ((1u << a.g_w[i]) - 1u)) << a.g_dst[i];
+    const IX tb0 = (IX)base << 12;
+    IX gib = tb0 ^ ti;
+    for (int i = 0; i < a.in_nq; ++i)
+        if ((tb0 >> a.in_q[i]) & 1u) gib ^= (IX)a.in_w[i];
+    const uint32_t asel0 = amp_sel(tb0, a.a_q, a.a_nt);
+    const uint32_t tsel0 = a.t_off >= 0 ? amp_sel(tb0, a.t_q, a.t_nt) : 0u;
+    for (int u = 0; u < (1 << a.h); ++u) {
+        const IX tb = tb0 ^ ((IX)a.hv[u] << 12);
+        const IX gi0 = gib ^ (IX)a.dgi[u];
         const IX go0 = tb | (IX)tid;
-        const int4* A = a.tab + a.a_off + ((size_t)amp_sel(tb, a.a_q, a.a_nt) << 12);
+        const int4* A = a.tab + a.a_off + ((size_t)(asel0 ^ a.dasel[u]) << 12);
         // per-tile factor: table T and the sign terms on tile bits
         int et = 0;
         for (int z = 0; z < a.ntz; ++z)
             if ((tb & (IX)a.tz[z].mask) == (IX)a.tz[z].vals) et += a.tz[z].e;
         const bool tf = a.t_off >= 0 || (et & 3) != 0;
         int4 f = make_int4(1 << 30, 0, 0, 0);   // 1 in split Q61
-        if (a.t_off >= 0) f = __ldg(a.tab + a.t_off + amp_sel(tb, a.t_q, a.t_nt));
+        if (a.t_off >= 0) f = __ldg(a.tab + a.t_off + (tsel0 ^ a.dtsel[u]));
         if (et & 3) {
             I2 v;
             v.x = ((long long)f.x << 31) + (long long)(unsigned)f.y;
@@ -1817,6 +1837,18 @@ __global__ void __launch_bounds__(512, 2) k_amp(const __grid_constant__ AmpArgs 
             v = mul_ik(v, et & 3);
             f = q61_split(v.x, v.y);
         }
+        // sign-term exponents of the thread's amplitudes (mod 4, as two
+        // bit planes over the registers)
+        uint32_t e0 = 0, e1 = 0;
+        for (int z = 0; z < a.nz; ++z)
+            if ((go0 & (IX)a.z4[z].mask) == (IX)a.z4[z].vals) {
+                const uint32_t J = a.z4j[z];
+                if (a.z4[z].e & 1) {
+                    e1 ^= e0 & J;
+                    e0 ^= J;
+                }
+                if (a.z4[z].e & 2) e1 ^= J;
+            }
         I2 x[NA];
 #pragma unroll
         for (int j = 0; j < NA; ++j) {
@@ -1834,15 +1866,9 @@ __global__ void __launch_bounds__(512, 2) k_amp(const __grid_constant__ AmpArgs 
 #pragma unroll
         for (int j = 0; j < NA; ++j) {
             const uint32_t l = tid | ((uint32_t)j << 9);
-            x[j] = qcmul(__ldg(A + l), x[j]);
-            if (tf) x[j] = qcmul(f, x[j]);
-            if (a.nz) {
-                const IX go = go0 | ((IX)j << 9);
-                int e = 0;
-                for (int z = 0; z < a.nz; ++z)
-                    if ((go & (IX)a.z4[z].mask) == (IX)a.z4[z].vals) e += a.z4[z].e;
-                x[j] = mul_ik(x[j], e & 3);
-            }
+            x[j] = qcmul_fast(__ldg(A + l), x[j]);
+            if (tf) x[j] = qcmul_fast(f, x[j]);
+            if (a.nz) x[j] = mul_ik(x[j], (int)(((e0 >> j) & 1u) | (((e1 >> j) & 1u) << 1)));
             long long vx = x[j].x, vy = x[j].y;
             if constexpr (QOUT == 0) {
                 __stcs(a.psi_out + (go0 | ((IX)j << 9)), make_double2(fix2d(vx, S), fix2d(vy, S)));
@@ -1857,7 +1883,8 @@ __global__ void __launch_bounds__(512, 2) k_amp(const __grid_constant__ AmpArgs 
                 __stcs(reinterpret_cast<longlong2*>(a.psi_out + (go0 | ((IX)j << 9))), make_longlong2(vx, vy));
             }
         }
-    }
+    }   // tiles of the group
+    }   // groups
 }
 
 }  // namespace mera
