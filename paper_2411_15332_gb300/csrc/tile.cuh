@@ -1849,6 +1849,8 @@ __global__ void __launch_bounds__(512, 2) k_amp(const __grid_constant__ AmpArgs 
                 }
                 if (a.z4[z].e & 2) e1 ^= J;
             }
+        // streaming loads (cached loads halve the DRAM re-reads of half
+        // rows but run slower: the pass is bound by its products)
         I2 x[NA];
 #pragma unroll
         for (int j = 0; j < NA; ++j) {
