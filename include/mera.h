@@ -133,6 +133,12 @@ int mera_state_set_basis(mera_state* s, uint64_t index);
 /* Copy 2^n amplitudes from / to host memory (pinned memory gives full
  * bandwidth).  Synchronous: returns after the copy completed. */
 int mera_state_copy_from_host(mera_state* s, const void* host);
+/* As mera_state_copy_from_host, but only enqueued on the state's stream:
+ * the call returns at once and the copy overlaps work on other streams
+ * (truly asynchronous for page-locked host memory).  The host buffer must
+ * stay valid and unchanged until the state's stream has passed the copy
+ * (mera_state_synchronize or any later synchronising call on the state). */
+int mera_state_copy_from_host_async(mera_state* s, const void* host);
 int mera_state_copy_to_host(mera_state* s, void* host);
 
 /* Read k amplitudes at basis indices idx[0..k-1] (host array) into

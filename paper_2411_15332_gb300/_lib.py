@@ -69,6 +69,7 @@ PROTOS = {
     "mera_state_copy_to_host": (I, [P, P]),
     "mera_state_get_amplitudes": (I, [P, U64P, SZ, DP]),
     "mera_state_synchronize": (I, [P]),
+    "mera_state_copy_from_host_async": (I, [P, P]),
     "mera_gate_matrix": (I, [I, DP, IP, DP]),
     "mera_apply_gate": (I, [P, I, IP, I, IP, I, DP]),
     "mera_apply_matrix": (I, [P, DP, IP, I, IP, I]),

@@ -81,6 +81,17 @@ class State:
             raise ValueError("wrong length")
         L.check(L.lib().mera_state_copy_from_host(self._h, C.c_void_p(a.ctypes.data)))
 
+    def from_host_async(self, psi):
+        """Enqueue the upload of ``psi`` (a contiguous array of the state's
+        complex dtype, ideally page-locked, e.g. a pinned torch tensor's
+        numpy view) on the state's stream and return at once; ``psi`` must
+        stay alive and unchanged until the stream has passed the copy."""
+        dt = np.complex128 if self.dtype == "c128" else np.complex64
+        if not isinstance(psi, np.ndarray) or psi.dtype != dt or psi.size != 1 << self.n or \
+                not psi.flags["C_CONTIGUOUS"]:
+            raise ValueError("psi must be a contiguous array of 2^n amplitudes of the state's dtype")
+        L.check(L.lib().mera_state_copy_from_host_async(self._h, C.c_void_p(psi.ctypes.data)))
+
     def to_numpy(self) -> np.ndarray:
         dt = np.complex128 if self.dtype == "c128" else np.complex64
         out = np.empty(1 << self.n, dtype=dt)

@@ -305,6 +305,15 @@ int mera_state_copy_from_host(mera_state* s, const void* host) {
     API_END
 }
 
+int mera_state_copy_from_host_async(mera_state* s, const void* host) {
+    API_BEGIN
+    MERA_TRY(check_state(s));
+    MERA_RETURN_IF(host == nullptr, MERA_EINVAL, "host is NULL");
+    MERA_CHECK_CUDA(cudaMemcpyAsync(s->data, host, num_amps(s) * elem_bytes(s->dtype), cudaMemcpyHostToDevice, s->stream));
+    return MERA_OK;
+    API_END
+}
+
 int mera_state_copy_to_host(mera_state* s, void* host) {
     API_BEGIN
     MERA_TRY(check_state(s));

@@ -85,3 +85,30 @@ def test_gather_amplitudes():
     s = new_state(n, "c128", psi)
     idx = np.array([0, 1, 5, 1000, (1 << n) - 1])
     assert np.array_equal(s.amplitudes(idx), psi[idx])
+
+
+def test_async_upload_overlaps_and_matches():
+    """mera_state_copy_from_host_async: two states on two streams, one
+    uploading while the other runs a circuit; both give the oracle's
+    result."""
+    import torch
+    from oracle import statevector as sv
+    from paper_2411_15332_gb300 import State, inputs
+    n = 16
+    ops = inputs.layered_circuit(n, 3, seed=5)
+    host = torch.zeros((1 << n) * 2, dtype=torch.float64).pin_memory()
+    host[0] = 1.0
+    hp = host.numpy().view(np.complex128)
+    a = State(n, stream=torch.cuda.Stream())
+    b = State(n, stream=torch.cuda.Stream())
+    a.from_host_async(hp)
+    a.apply_circuit(ops, mode="fused")
+    b.from_host_async(hp)
+    b.apply_circuit(ops, mode="fused")
+    ref = sv.simulate(n, ops)
+    for s in (a, b):
+        got = s.to_numpy()
+        assert np.max(np.abs(got - ref)) <= 1e-12
+        s.close()
+    with pytest.raises(ValueError):
+        State(n).from_host_async(np.zeros(1 << n, dtype=np.complex64))
