@@ -453,13 +453,17 @@ static bool amp_layout(const AmpRun& r, AmpLayout& L) {
 
 // The longest affine monomial run starting at ops[pos], shortened until
 // its diagonal fits the layout.
+static constexpr size_t AMP_MAX_RUN = 2048;   // gates per run (bounds the planning work)
 static AmpRun amp_grow(const std::vector<PrepOp>& ops, const std::vector<int>& order, size_t pos, int n) {
     AmpRun r(n);
-    for (size_t k = pos; k < order.size(); ++k) {
+    for (size_t k = pos; k < order.size() && r.ops.size() < AMP_MAX_RUN; ++k) {
         AmpRun next = r;
         if (!next.take(ops, order[k])) break;
-        AmpLayout L;
-        if (!amp_layout(next, L)) break;
+        // only a new multi-qubit term can change the layout's feasibility
+        if (next.terms.size() != r.terms.size()) {
+            AmpLayout L;
+            if (!amp_layout(next, L)) break;
+        }
         r = std::move(next);
     }
     return r;
@@ -2380,8 +2384,15 @@ int fused_launch(const FusedPlan<V>& plan, size_t i, PassArgs<V>& A, unsigned ny
         const uint64_t ctas = std::max<uint64_t>(1, std::min<uint64_t>(g.ngroups, 16ull * (uint64_t)sms));
         void* args[] = {&g};
         launch_begin(st, MERA_KCLASS_AMP, pass_bytes);
-        MERA_CHECK_CUDA(cudaLaunchKernel(tile_fn_amp(A.q_in, A.q_out, plan.n > 32 ? 1 : 0), dim3((unsigned)ctas, 1),
-                                         dim3(512), args, 0, st));
+        // 64-bit index arithmetic above 2^32 amplitudes (MERA_AMP_IX64=1
+        // forces it, to test that variant on small states)
+        static int ix64 = -1;
+        if (ix64 < 0) {
+            const char* e = getenv("MERA_AMP_IX64");
+            ix64 = (e && atoi(e) == 1) ? 1 : 0;
+        }
+        MERA_CHECK_CUDA(cudaLaunchKernel(tile_fn_amp(A.q_in, A.q_out, (plan.n > 32 || ix64) ? 1 : 0),
+                                         dim3((unsigned)ctas, 1), dim3(512), args, 0, st));
         return launch_end(st);
     }
     if (sizeof(V) == 16 && ny == 1 && plan.dpass[i]) {

@@ -168,3 +168,32 @@ def test_run_of_monomial_passes_after_a_per_gate_op(layers):
     ref = sv.apply_matrix(ref, n, perm8, (9, 2, 13))
     ref = sv.simulate(n, body, psi0=ref)
     assert max_err(got, ref) <= TOL
+
+
+def test_64bit_index_variant(tmp_path):
+    """The variant with 64-bit index arithmetic (states above 2^32
+    amplitudes) on a small state (MERA_AMP_IX64=1, another process)
+    gives the same bits as the 32-bit one."""
+    n = 18
+    rng = np.random.default_rng(11)
+    ops = inputs.hadamard_all(n)
+    for _ in range(2):
+        ops += _monomial_run(rng, n, 30, 30)
+    got = _run(n, ops)
+    import pickle
+    out = tmp_path / "ix64.npy"
+    ops_file = tmp_path / "ops.pkl"
+    with open(ops_file, "wb") as f:
+        pickle.dump(ops, f)
+    code = ("import pickle\n"
+            "import numpy as np\n"
+            "from paper_2411_15332_gb300 import core\n"
+            f"ops = pickle.load(open({str(ops_file)!r}, 'rb'))\n"
+            f"s = core.State({n})\n"
+            "s.apply_circuit(ops, mode='fused')\n"
+            f"np.save({str(out)!r}, s.to_numpy())\n")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    subprocess.run([sys.executable, "-c", code], cwd=root, env={**os.environ, "MERA_AMP_IX64": "1"}, check=True,
+                   timeout=600)
+    assert np.array_equal(got.view(np.uint64), np.load(out).view(np.uint64))
+    assert max_err(got, sv.simulate(n, ops)) <= TOL
