@@ -2256,22 +2256,6 @@ int fused_build(int n, const std::vector<PrepOp>& ops, FusedPlan<V>& plan, bool 
             if (ok) dpass_args(A, n, plan.dargs[i]);
         }
     }
-    // A plan made only of per-tile int64 Hadamard passes (Grover-type
-    // circuits) takes 2^13-amplitude tiles (512 threads, one CTA per SM)
-    // when that saves passes: one more butterfly level per HBM round trip
-    if (sizeof(V) == 16 && kforce == 0 && plan.K == 12 && n >= 14 && !getenv("MERA_TILE_BITS")) {
-        auto all_hp = [](const FusedPlan<V>& p) {
-            bool all = !p.args.empty();
-            for (size_t i = 0; i < p.args.size() && all; ++i) all = p.single[i] < 0 && p.hpass[i] && p.eng[i] == ENG_I64;
-            return all;
-        };
-        if (all_hp(plan)) {
-            FusedPlan<V> wide;
-            if (fused_build<V>(n, ops, wide, fp_only, resident_ok, 13, amp_ok) == MERA_OK && all_hp(wide) &&
-                wide.args.size() < plan.args.size())
-                plan = std::move(wide);
-        }
-    }
     return MERA_OK;
 }
 

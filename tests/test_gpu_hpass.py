@@ -136,3 +136,26 @@ def test_bulk_shortfall_hook_validates():
     assert L.lib().mera_test_bulk_shortfall(8) == L.MERA_EINVAL
     assert L.lib().mera_test_bulk_shortfall(8192) == L.MERA_EINVAL
     assert L.lib().mera_test_bulk_shortfall(0) == L.MERA_OK
+
+
+def test_thirteen_bit_tiles(tmp_path):
+    """MERA_TILE_BITS=13 (another process): 2^13-amplitude tiles, the
+    512-thread variant of the kernel, one CTA per SM; same result as the
+    oracle."""
+    import os
+    import subprocess
+    import sys
+    n = 17
+    ops, _ = inputs.grover_circuit(n, 2, seed=3)
+    out = tmp_path / "k13.npy"
+    code = ("import numpy as np\n"
+            "from paper_2411_15332_gb300 import inputs, core\n"
+            f"ops, _ = inputs.grover_circuit({n}, 2, seed=3)\n"
+            f"assert core.plan_summary({n}, ops).startswith('K=13')\n"
+            f"s = core.State({n})\n"
+            "s.apply_circuit(ops, mode='fused')\n"
+            f"np.save({str(out)!r}, s.to_numpy())\n")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    subprocess.run([sys.executable, "-c", code], cwd=root, env={**os.environ, "MERA_TILE_BITS": "13"}, check=True,
+                   timeout=600)
+    assert max_err(np.load(out), sv.simulate(n, ops)) <= 1e-13

@@ -245,7 +245,7 @@ def test_bulk_staging_eligibility(core):
     ops, _ = inputs.grover_circuit(33, 8, seed=3)
     passes = core.plan_summary(33, ops).splitlines()[1:]
     bulk = [p for p in passes if " bulk" in p]
-    assert len(bulk) >= 40
+    assert len(bulk) >= 30
     for p in bulk:
         assert "pipelined" in p and "tile={0,1,2," in p
     # pass 0 starts with H on qubits 0..3: phase 0 has register bits 0..2
