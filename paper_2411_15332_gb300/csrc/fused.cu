@@ -459,11 +459,9 @@ static AmpRun amp_grow(const std::vector<PrepOp>& ops, const std::vector<int>& o
     for (size_t k = pos; k < order.size() && r.ops.size() < AMP_MAX_RUN; ++k) {
         AmpRun next = r;
         if (!next.take(ops, order[k])) break;
-        // only a new multi-qubit term can change the layout's feasibility
-        if (next.terms.size() != r.terms.size()) {
-            AmpLayout L;
-            if (!amp_layout(next, L)) break;
-        }
+        // a new term or a factor on another tile qubit may overflow the tables
+        AmpLayout L;
+        if (!amp_layout(next, L)) break;
         r = std::move(next);
     }
     return r;
@@ -2551,7 +2549,14 @@ static bool ensure_pong(mera_state* s) {
 // second buffer they write into is there.
 template <typename V>
 static int build_for_state(mera_state* s, const std::vector<PrepOp>& ops, FusedPlan<V>& plan) {
-    MERA_TRY(fused_build<V>(s->n, ops, plan, false, true, 0, !s->pong_failed));
+    // monomial run passes only if a second state buffer exists or fits
+    bool room = !s->pong_failed;
+    if (room && s->pong_bytes < num_amps(s) * elem_bytes(s->dtype)) {
+        size_t fr = 0, tot = 0;
+        room = cudaMemGetInfo(&fr, &tot) == cudaSuccess && fr > num_amps(s) * elem_bytes(s->dtype) + (1ull << 30);
+        cudaGetLastError();
+    }
+    MERA_TRY(fused_build<V>(s->n, ops, plan, false, true, 0, room));
     bool any = false;
     for (unsigned char a : plan.amp) any = any || a;
     if (any && !ensure_pong(s)) {

@@ -252,3 +252,16 @@ def test_bulk_staging_eligibility(core):
     assert " bulk" not in passes[0]
     for p in core.plan_summary(30, inputs.layered_circuit(30, 20, seed=2)).splitlines()[1:]:
         assert " bulk" not in p or "pipelined" in p
+
+
+def test_monomial_runs_respect_table_limits_at_n34(core):
+    """With 22 tile qubits the per-qubit phases of a layer may not all fit
+    table A's selection and table T: runs are cut so that T keeps at most 16
+    qubits and A selects at most 8 (the plan as described assumes room for
+    the second buffer)."""
+    summary = core.plan_summary(34, inputs.layered_circuit(34, 20, seed=2))
+    amp = [l for l in summary.splitlines()[1:] if " amp " in l]
+    assert len(amp) >= 20
+    for l in amp:
+        assert int(re.search(r"tile_tab=(\d+)", l).group(1)) <= 16
+        assert int(re.search(r"sel_a=(\d+)", l).group(1)) <= 8
