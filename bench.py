@@ -795,8 +795,9 @@ def run_mera(args, rank, world, local_rank):
             # upload (asynchronous, pinned) overlapping this step's circuit;
             # every step still uploads its input and reads its result
             e2e_s = None
+            sts = [st]
             try:
-                sts = [st, mera.State(n, args.dtype, stream=torch.cuda.Stream())]
+                sts.append(mera.State(n, args.dtype, stream=torch.cuda.Stream()))
                 st.set_stream(torch.cuda.Stream())
                 for s2 in sts:   # warm both plans
                     s2.from_host_async(hp)
@@ -812,9 +813,14 @@ def run_mera(args, rank, world, local_rank):
                         nxt.from_host_async(hp)
                     cur.observables(0)
                 e2e_s = (time.perf_counter() - t0) / args.steps
-                sts[1].close()
-            except Exception as ex:   # no room for a second state: sequential only
-                e2e_err = str(ex)[:200]
+            except Exception:   # no room for a second state: sequential only
+                e2e_s = None
+            finally:
+                if len(sts) > 1:   # release the second state and its memory
+                    sts[1].close()
+                    sts[1].tensor = None
+                del sts
+                _free_cuda()
             e2e = {"value": upd * world / (e2e_s or seq_s), "unit": METRIC,
                    "h2d_bytes_per_step": (1 << n) * eb + ops_bytes, "d2h_bytes_per_step": 24,
                    "seconds_per_step": e2e_s or seq_s,
