@@ -1868,8 +1868,8 @@ __global__ void __launch_bounds__(512, 2) k_amp(const __grid_constant__ AmpArgs 
 #pragma unroll
         for (int j = 0; j < NA; ++j) {
             const uint32_t l = tid | ((uint32_t)j << 9);
-            x[j] = qcmul_fast(__ldg(A + l), x[j]);
-            if (tf) x[j] = qcmul_fast(f, x[j]);
+            x[j] = qcmul4_fast(__ldg(A + l), x[j]);
+            if (tf) x[j] = qcmul4_fast(f, x[j]);
             if (a.nz) x[j] = mul_ik(x[j], (int)(((e0 >> j) & 1u) | (((e1 >> j) & 1u) << 1)));
             long long vx = x[j].x, vy = x[j].y;
             if constexpr (QOUT == 0) {
