@@ -430,8 +430,7 @@ def _section_statevector(name, n, mode, steps, warmup, peak, peak_kind, check):
 
     def step():
         st.set_basis(0)
-        st.apply_circuit(ops, mode=mode)
-        return st.observables(0)
+        return st.apply_circuit_observe(ops, 0, mode=mode)
 
     ms, prof, launches, obs = _time_steps(step, steps, warmup, stream)
     table = _kernel_table(prof, ms * steps, peak)
@@ -737,8 +736,9 @@ def run_mera(args, rank, world, local_rank):
 
     def step():
         st.set_basis(0)
-        st.apply_circuit(ops, mode=args.mode)
-        return st.observables(0)
+        # the circuit and its readout (norm^2, <Z_0>) in one call: the last
+        # pass sums the readout while it writes the state where it can
+        return st.apply_circuit_observe(ops, 0, mode=args.mode)
 
     for _ in range(max(args.warmup, 0)):
         obs = step()
@@ -781,14 +781,12 @@ def run_mera(args, rank, world, local_rank):
             host[0] = 1.0
             hp = host.numpy().view(np.complex128 if eb == 16 else np.complex64)
             st.from_numpy(hp)
-            st.apply_circuit(ops, mode=args.mode)
-            st.observables(0)
+            st.apply_circuit_observe(ops, 0, mode=args.mode)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             for _ in range(args.steps):
-                st.from_numpy(hp)                       # H2D of the input state
-                st.apply_circuit(ops, mode=args.mode)   # ops table is copied per launch
-                st.observables(0)                       # D2H of the result
+                st.from_numpy(hp)                                # H2D of the input state
+                st.apply_circuit_observe(ops, 0, mode=args.mode)  # ops table copied; D2H of the result
             seq_s = (time.perf_counter() - t0) / args.steps
             ops_bytes = 80 * len(ops)
             # pipelined: two states on two streams, the next step's input
@@ -801,17 +799,17 @@ def run_mera(args, rank, world, local_rank):
                 st.set_stream(torch.cuda.Stream())
                 for s2 in sts:   # warm both plans
                     s2.from_host_async(hp)
-                    s2.apply_circuit(ops, mode=args.mode)
-                    s2.observables(0)
+                    s2.apply_circuit_observe(ops, 0, mode=args.mode)
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 sts[0].from_host_async(hp)
                 for k in range(args.steps):
                     cur, nxt = sts[k % 2], sts[(k + 1) % 2]
-                    cur.apply_circuit(ops, mode=args.mode)
+                    # enqueue the next step's upload first: the readout's
+                    # synchronisation then waits only for this state's stream
                     if k + 1 < args.steps:
                         nxt.from_host_async(hp)
-                    cur.observables(0)
+                    cur.apply_circuit_observe(ops, 0, mode=args.mode)
                 e2e_s = (time.perf_counter() - t0) / args.steps
             except Exception:   # no room for a second state: sequential only
                 e2e_s = None

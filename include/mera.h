@@ -177,6 +177,15 @@ int mera_apply_matrix(mera_state* s, const double* matrix, const int* targets, i
  * and the amplitudes are then not valid. */
 int mera_apply_circuit(mera_state* s, const mera_op* ops, size_t nops, int mode);
 
+/* mera_apply_circuit followed by mera_observables(s, q, out): the circuit,
+ * then out[0] = norm^2, out[1] = <Z_q>, out[2] = sum over qubits of <Z_q>
+ * (Eq. 4-5), summed in float64.  In MERA_MODE_FUSED, when the circuit's
+ * last pass is a monomial run pass that writes the state as doubles, that
+ * pass sums the readout while it stores the amplitudes (no further read of
+ * the state); otherwise the readout reduction runs after the circuit.
+ * Synchronises the state's stream; q out of range is MERA_EINVAL. */
+int mera_apply_circuit_observe(mera_state* s, const mera_op* ops, size_t nops, int mode, int q, double out[3]);
+
 /* Describe how MERA_MODE_FUSED would run ops[0..nops-1] on n qubits of
  * `dtype`, without touching a GPU: a header line (tile bits, passes,
  * whether the complex128 state stays int64 fixed point across passes),

@@ -74,6 +74,7 @@ PROTOS = {
     "mera_apply_gate": (I, [P, I, IP, I, IP, I, DP]),
     "mera_apply_matrix": (I, [P, DP, IP, I, IP, I]),
     "mera_apply_circuit": (I, [P, P, SZ, I]),
+    "mera_apply_circuit_observe": (I, [P, P, SZ, I, I, DP]),
     "mera_hadamard_layer": (I, [P, U64]),
     "mera_plan_summary": (I, [I, I, P, SZ, C.c_char_p, SZ, IP]),
     "mera_norm2": (I, [P, DP]),

@@ -129,6 +129,17 @@ class State:
         L.check(L.lib().mera_apply_circuit(self._h, C.c_void_p(arr.ctypes.data), len(arr), md))
         del keep
 
+    def apply_circuit_observe(self, ops, q: int = 0, mode: str = "fused"):
+        """apply_circuit then observables(q) in one call: (norm^2, <Z_q>,
+        sum_q <Z_q>).  In fused mode the circuit's last pass sums the readout
+        while it writes the state when it can (see mera_apply_circuit_observe)."""
+        arr, keep = L.ops_to_array(ops)
+        md = L.MODE_FUSED if mode == "fused" else L.MODE_PER_GATE
+        out = (C.c_double * 3)()
+        L.check(L.lib().mera_apply_circuit_observe(self._h, C.c_void_p(arr.ctypes.data), len(arr), md, int(q), out))
+        del keep
+        return tuple(out)
+
     def hadamard_layer(self, mask: int):
         """H on every qubit in ``mask`` (the RH structure, Sec. III-B)."""
         L.check(L.lib().mera_hadamard_layer(self._h, int(mask)))

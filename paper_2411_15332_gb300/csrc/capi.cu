@@ -418,6 +418,19 @@ int mera_apply_circuit(mera_state* s, const mera_op* ops, size_t nops, int mode)
     API_END
 }
 
+int mera_apply_circuit_observe(mera_state* s, const mera_op* ops, size_t nops, int mode, int q, double out[3]) {
+    API_BEGIN
+    MERA_TRY(check_state(s));
+    MERA_RETURN_IF(nops > 0 && ops == nullptr, MERA_EINVAL, "ops is NULL");
+    MERA_RETURN_IF(out == nullptr, MERA_EINVAL, "out is NULL");
+    MERA_RETURN_IF(q < 0 || q >= s->n, MERA_EINVAL, "qubit %d out of range", q);
+    MERA_RETURN_IF(mode != MERA_MODE_PER_GATE && mode != MERA_MODE_FUSED, MERA_EINVAL, "unknown mode %d", mode);
+    if (mode == MERA_MODE_FUSED) return apply_fused_circuit_observe(s, ops, nops, q, out);
+    MERA_TRY(mera_apply_circuit(s, ops, nops, mode));
+    return observables(s, q, out);
+    API_END
+}
+
 int mera_plan_summary(int n, int dtype, const mera_op* ops, size_t nops, char* out, size_t cap, int* npasses) {
     API_BEGIN
     MERA_RETURN_IF(n < 5 || n > MERA_MAX_QUBITS, MERA_EINVAL, "n=%d outside [5, %d] for the fused path", n,

@@ -135,6 +135,10 @@ int apply_fused(mera_state* s, const std::vector<PrepOp>& ops);
 // Fused path for a raw op list: a circuit identical to the previous fused
 // circuit of the state reuses its passes and device tables.
 int apply_fused_circuit(mera_state* s, const mera_op* ops, size_t nops);
+// The same, then the readouts of observables() for qubit q into out[3]
+// (host): summed by the circuit's last pass where it is a monomial run
+// pass writing doubles, else by the readout reduction afterwards.
+int apply_fused_circuit_observe(mera_state* s, const mera_op* ops, size_t nops, int q, double out[3]);
 void fused_cache_free(mera_state* s);
 void fused_set_bulk_shortfall(unsigned bytes);
 int plan_summary(int n, int dtype, const std::vector<PrepOp>& ops, std::string* out, int* npasses);

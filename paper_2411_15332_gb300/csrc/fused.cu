@@ -26,11 +26,15 @@
 
 #include "common.cuh"
 #include "fused.cuh"
+#include "reduce.cuh"
 #include "tile_fns.cuh"
 
 namespace mera {
 
 static int popc(uint64_t x) { return __builtin_popcountll(x); }
+
+// Partial triples a readout summed by the last pass may write (its CTAs).
+static constexpr int RD_MAX_PARTIALS = 4096;
 
 int fused_tile_bits(int dtype, int n) {
     int K = dtype == MERA_C128 ? 12 : 13;
@@ -2373,7 +2377,16 @@ int fused_launch(const FusedPlan<V>& plan, size_t i, PassArgs<V>& A, unsigned ny
             const char* e = getenv("MERA_AMP_IX64");
             ix64 = (e && atoi(e) == 1) ? 1 : 0;
         }
-        MERA_CHECK_CUDA(cudaLaunchKernel(tile_fn_amp(A.q_in, A.q_out, (plan.n > 32 || ix64) ? 1 : 0),
+        const int wide = (plan.n > 32 || ix64) ? 1 : 0;
+        // the circuit's last pass, writing doubles, may sum the readout
+        const bool rd = plan.rd_partial && !A.q_out && i + 1 == plan.args.size() && ctas <= RD_MAX_PARTIALS;
+        if (rd) {
+            g.rd_partial = plan.rd_partial;
+            g.rd_q = plan.rd_q;
+            g.rd_n = plan.n;
+            plan.rd_nb = (int)ctas;
+        }
+        MERA_CHECK_CUDA(cudaLaunchKernel(rd ? tile_fn_amp_readout(A.q_in, wide) : tile_fn_amp(A.q_in, A.q_out, wide),
                                          dim3((unsigned)ctas, 1), dim3(512), args, 0, st));
         return launch_end(st);
     }
@@ -2567,7 +2580,23 @@ static int build_for_state(mera_state* s, const std::vector<PrepOp>& ops, FusedP
 }
 
 template <typename V>
-static int launch_plan(mera_state* s, FusedPlan<V>& plan, const std::vector<PrepOp>& ops) {
+static int launch_plan_passes(mera_state* s, FusedPlan<V>& plan, const std::vector<PrepOp>& ops);
+
+template <typename V>
+static int launch_plan(mera_state* s, FusedPlan<V>& plan, const std::vector<PrepOp>& ops, double* rd_partial = nullptr,
+                       int rd_q = 0, int* rd_nb = nullptr) {
+    // a requested readout rides on the last pass where it can (plan.rd_nb > 0)
+    plan.rd_partial = rd_partial;
+    plan.rd_q = rd_q;
+    plan.rd_nb = 0;
+    const int st = launch_plan_passes<V>(s, plan, ops);
+    plan.rd_partial = nullptr;
+    if (rd_nb) *rd_nb = plan.rd_nb;
+    return st;
+}
+
+template <typename V>
+static int launch_plan_passes(mera_state* s, FusedPlan<V>& plan, const std::vector<PrepOp>& ops) {
     if (plan.resident || plan.efmt) {
         MERA_TRY(state_ensure_scratch(s, 16384));
         MERA_TRY(qscale_launch(s->data, s->n, s->scratch, s->stream));
@@ -2649,12 +2678,17 @@ static std::vector<unsigned char> circuit_key(const mera_state* s, const mera_op
     return k;
 }
 
-int apply_fused_circuit(mera_state* s, const mera_op* ops, size_t nops) {
+// Scratch layout of a readout requested with a fused circuit: above the
+// norm-bound partials and the resident scale (bytes 0..16 KiB).
+static constexpr size_t RD_SCRATCH_OFF = 16384;
+
+static int apply_fused_circuit_rd(mera_state* s, const mera_op* ops, size_t nops, double* rd_partial, int rd_q,
+                                  int* rd_nb) {
     FusedCache* c = reinterpret_cast<FusedCache*>(s->fused_cache);
     std::vector<unsigned char> key = circuit_key(s, ops, nops);
     if (c && c->key == key) {
-        if (s->dtype == MERA_C128) return launch_plan<double2>(s, c->p128, c->ops);
-        return launch_plan<float2>(s, c->p64, c->ops);
+        if (s->dtype == MERA_C128) return launch_plan<double2>(s, c->p128, c->ops, rd_partial, rd_q, rd_nb);
+        return launch_plan<float2>(s, c->p64, c->ops, rd_partial, rd_q, rd_nb);
     }
     std::vector<PrepOp> prep(nops);
     for (size_t j = 0; j < nops; ++j) {
@@ -2683,8 +2717,26 @@ int apply_fused_circuit(mera_state* s, const mera_op* ops, size_t nops) {
     }
     c->key.swap(key);
     s->fused_cache = c;
-    if (s->dtype == MERA_C128) return launch_plan<double2>(s, c->p128, c->ops);
-    return launch_plan<float2>(s, c->p64, c->ops);
+    if (s->dtype == MERA_C128) return launch_plan<double2>(s, c->p128, c->ops, rd_partial, rd_q, rd_nb);
+    return launch_plan<float2>(s, c->p64, c->ops, rd_partial, rd_q, rd_nb);
+}
+
+int apply_fused_circuit(mera_state* s, const mera_op* ops, size_t nops) {
+    return apply_fused_circuit_rd(s, ops, nops, nullptr, 0, nullptr);
+}
+
+int apply_fused_circuit_observe(mera_state* s, const mera_op* ops, size_t nops, int q, double out[3]) {
+    const size_t np = 3 * (size_t)std::max(RD_MAX_PARTIALS, reduce_blocks(num_amps(s)));
+    MERA_TRY(state_ensure_scratch(s, RD_SCRATCH_OFF + (np + 8) * sizeof(double)));
+    double* partial = reinterpret_cast<double*>(reinterpret_cast<char*>(s->scratch) + RD_SCRATCH_OFF);
+    double* out_dev = partial + np;
+    int nb = 0;
+    MERA_TRY(apply_fused_circuit_rd(s, ops, nops, partial, q, &nb));
+    if (nb > 0) MERA_TRY(observables_finish(s, partial, nb, out_dev));
+    else MERA_TRY(observables_device(s, q, partial, out_dev));
+    MERA_CHECK_CUDA(cudaMemcpyAsync(out, out_dev, 3 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    MERA_CHECK_CUDA(cudaStreamSynchronize(s->stream));
+    return state_check_waits(s);
 }
 
 // Host-only description of the plan (no device work).

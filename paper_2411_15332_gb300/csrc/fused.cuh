@@ -26,6 +26,11 @@ struct FusedPlan {
     bool efmt = false;                    // ENG_I64 Hadamard runs keep per-amplitude exponents between passes
     bool bulk = false;                    // some Hadamard pass stages its tiles with bulk copies
     int* wait_flag = nullptr;             // device int the bulk-copy waits set when they run out (set at launch)
+    // readout summed by the last pass (set at launch; rd_nb receives the
+    // number of partial triples written, 0 if the last pass cannot)
+    double* rd_partial = nullptr;
+    int rd_q = 0;
+    mutable int rd_nb = 0;
 };
 
 // fp_only: every pass in the float engine (coefficients as plain values).

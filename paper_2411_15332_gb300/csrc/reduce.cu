@@ -241,6 +241,12 @@ static int observables_t(mera_state* s, int q, double* partial, double* out_dev)
     return launch_end(s->stream);
 }
 
+int observables_finish(mera_state* s, const double* partial, int nb, double* out_dev) {
+    launch_begin(s->stream, MERA_KCLASS_REDUCE, 24.0 * nb);
+    k_finish3<<<1, 256, 0, s->stream>>>(partial, nb, out_dev);
+    return launch_end(s->stream);
+}
+
 int observables_device(mera_state* s, int q, double* partial, double* out_dev) {
     if (s->dtype == MERA_C128) return observables_t<double2>(s, q, partial, out_dev);
     return observables_t<float2>(s, q, partial, out_dev);

@@ -1786,6 +1786,11 @@ struct AmpArgs {
     int g_nruns;
     uint32_t g_src[8], g_w[8], g_dst[8];
     int nperm, ndiag;              // the run's gates (description only)
+    // readout in the pass that writes doubles (RD variant): per CTA the
+    // partial sums of |a|^2, (1 - 2 bit_q) |a|^2 and (n - 2 popcount) |a|^2
+    // of the amplitudes it stores, in float64
+    double* rd_partial;
+    int rd_q, rd_n;
 };
 
 __device__ __forceinline__ uint32_t amp_sel(unsigned long long v, const int8_t* q, int nt) {
@@ -1798,10 +1803,12 @@ __device__ __forceinline__ int4 q61_split(long long re, long long im) {
                      (int)((unsigned)im & 0x7FFFFFFFu));
 }
 
-template <int QIN, int QOUT, typename IX>
+template <int QIN, int QOUT, typename IX, int RD = 0>
 __global__ void __launch_bounds__(512, 2) k_amp(const __grid_constant__ AmpArgs a) {
+    static_assert(RD == 0 || QOUT == 0, "the readout variant writes doubles");
     constexpr int NA = 1 << DPASS_RBITS;
     const uint32_t tid = threadIdx.x;
+    double r0 = 0.0, r1 = 0.0, r2 = 0.0;   // readout sums (RD)
     IX ti = (IX)a.in_c;
 #pragma unroll
     for (int t = 0; t < DPASS_TBITS; ++t) ti ^= ((IX)0 - (IX)((tid >> t) & 1u)) & (IX)a.in_t[t];
@@ -1873,7 +1880,15 @@ __global__ void __launch_bounds__(512, 2) k_amp(const __grid_constant__ AmpArgs 
             if (a.nz) x[j] = mul_ik(x[j], (int)(((e0 >> j) & 1u) | (((e1 >> j) & 1u) << 1)));
             long long vx = x[j].x, vy = x[j].y;
             if constexpr (QOUT == 0) {
-                __stcs(a.psi_out + (go0 | ((IX)j << 9)), make_double2(fix2d(vx, S), fix2d(vy, S)));
+                const double dx = fix2d(vx, S), dy = fix2d(vy, S);
+                const IX go = go0 | ((IX)j << 9);
+                __stcs(a.psi_out + go, make_double2(dx, dy));
+                if constexpr (RD == 1) {
+                    const double p = fma(dx, dx, dy * dy);
+                    r0 += p;
+                    if (((unsigned long long)go >> a.rd_q) & 1ull) r1 += p;
+                    r2 = fma((double)__popcll((unsigned long long)go), p, r2);
+                }
             } else {
                 if (k > 0) {
                     vx = (vx + half) >> k;
@@ -1887,6 +1902,40 @@ __global__ void __launch_bounds__(512, 2) k_amp(const __grid_constant__ AmpArgs 
         }
     }   // tiles of the group
     }   // groups
+    if constexpr (RD == 1) {
+        // fixed-order block sums: warps by shuffles, then warp 0
+        __shared__ double sh[3][16];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            r0 += __shfl_down_sync(0xffffffffu, r0, o);
+            r1 += __shfl_down_sync(0xffffffffu, r1, o);
+            r2 += __shfl_down_sync(0xffffffffu, r2, o);
+        }
+        const int w = (int)(tid >> 5), l = (int)(tid & 31u);
+        if (l == 0) {
+            sh[0][w] = r0;
+            sh[1][w] = r1;
+            sh[2][w] = r2;
+        }
+        __syncthreads();
+        if (w == 0) {
+            r0 = l < 16 ? sh[0][l] : 0.0;
+            r1 = l < 16 ? sh[1][l] : 0.0;
+            r2 = l < 16 ? sh[2][l] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                r0 += __shfl_down_sync(0xffffffffu, r0, o);
+                r1 += __shfl_down_sync(0xffffffffu, r1, o);
+                r2 += __shfl_down_sync(0xffffffffu, r2, o);
+            }
+            if (l == 0) {
+                // <Z_q> = norm - 2 mass(bit q = 1); sum_q <Z_q> = n norm - 2 sum popcount |a|^2
+                a.rd_partial[3 * blockIdx.x + 0] = r0;
+                a.rd_partial[3 * blockIdx.x + 1] = r0 - 2.0 * r1;
+                a.rd_partial[3 * blockIdx.x + 2] = (double)a.rd_n * r0 - 2.0 * r2;
+            }
+        }
+    }
 }
 
 }  // namespace mera

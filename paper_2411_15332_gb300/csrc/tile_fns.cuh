@@ -15,6 +15,8 @@ const void* tile_fn_q(int feat, int qin);
 const void* tile_fn_dpass(int wide);
 // affine monomial run pass: qin / qout = 1 for the resident format (0: doubles)
 const void* tile_fn_amp(int qin, int qout, int wide);
+// the same pass writing doubles and summing the readout (AmpArgs::rd_*)
+const void* tile_fn_amp_readout(int qin, int wide);
 const void* tile_fn_i64(int feat, int qin);
 // the Hadamard-pass kernel (ENG_I64 or ENG_Q): qin = 1 when the pass reads
 // doubles, qout = 1 when it writes the engine's own format (ENG_Q: global

@@ -16,6 +16,10 @@ static const void* amp_fn(int qin, int qout) {
 const void* tile_fn_amp(int qin, int qout, int wide) {
     return wide ? amp_fn<unsigned long long>(qin, qout) : amp_fn<uint32_t>(qin, qout);
 }
+const void* tile_fn_amp_readout(int qin, int wide) {
+    if (wide) return qin ? (const void*)k_amp<1, 0, unsigned long long, 1> : (const void*)k_amp<0, 0, unsigned long long, 1>;
+    return qin ? (const void*)k_amp<1, 0, uint32_t, 1> : (const void*)k_amp<0, 0, uint32_t, 1>;
+}
 
 const void* tile_fn_q(int feat, int qin) {
     if (qin) {

@@ -112,3 +112,86 @@ def test_async_upload_overlaps_and_matches():
         s.close()
     with pytest.raises(ValueError):
         State(n).from_host_async(np.zeros(1 << n, dtype=np.complex64))
+
+
+def _readouts(psi, n, q):
+    """norm^2, <Z_q> and sum_q <Z_q> of a state vector (numpy, float64)."""
+    p = np.abs(np.asarray(psi, dtype=np.complex128)) ** 2
+    idx = np.arange(p.size, dtype=np.uint64)
+    bit = ((idx >> np.uint64(q)) & np.uint64(1)).astype(bool)
+    pc = np.array([bin(i).count("1") for i in range(p.size)], dtype=np.float64)
+    return float(p.sum()), float(p[~bit].sum() - p[bit].sum()), float((p * (n - 2.0 * pc)).sum())
+
+
+def _check_readout(got, ref, n, dtype="c128"):
+    from tests.gpu_helpers import obs_tol
+    assert abs(got[0] - ref[0]) <= obs_tol(dtype, 1.0)
+    assert abs(got[1] - ref[1]) <= obs_tol(dtype, 1.0)
+    assert abs(got[2] - ref[2]) <= obs_tol(dtype, float(n))
+
+
+@pytest.mark.parametrize("q", [0, 4, 9, 12, 15])
+def test_apply_circuit_observe_in_the_last_pass(q):
+    """mera_apply_circuit_observe on a layered circuit: the last pass (a
+    monomial run pass writing doubles) sums the readout while it stores the
+    state.  Same state as mera_apply_circuit; readouts as mera_observables
+    and as the oracle's."""
+    from paper_2411_15332_gb300 import core
+    n = 16
+    ops = inputs.layered_circuit(n, 4, seed=21)
+    last = core.plan_summary(n, ops).splitlines()[-1]
+    assert " amp " in last and "q_out=0" in last
+    a = new_state(n)
+    got = a.apply_circuit_observe(ops, q)
+    b = new_state(n)
+    b.apply_circuit(ops, mode="fused")
+    ref = b.observables(q)
+    psi = a.to_numpy()
+    assert np.array_equal(psi, b.to_numpy())
+    a.close()
+    b.close()
+    _check_readout(got, ref, n)
+    _check_readout(got, _readouts(sv.simulate(n, ops), n, q), n)
+    # a second call on the same state (cached passes) gives the same sums
+    c = new_state(n)
+    c.apply_circuit_observe(ops, q)
+    c.set_basis(0)
+    assert c.apply_circuit_observe(ops, q) == got
+    c.close()
+
+
+@pytest.mark.parametrize("case", ["grover", "per_gate", "c64"])
+def test_apply_circuit_observe_without_a_readout_pass(case):
+    """Where the last pass cannot sum the readout (a Hadamard pass, the
+    per-gate mode, a complex64 state) the readout reduction runs after the
+    circuit: the results equal mera_observables'."""
+    n = 14
+    dtype, mode = "c128", "fused"
+    if case == "grover":
+        ops = inputs.grover_circuit(n, 2, seed=3)[0]
+    else:
+        ops = inputs.layered_circuit(n, 3, seed=5)
+        if case == "per_gate":
+            mode = "per_gate"
+        else:
+            dtype = "c64"
+    q = 3
+    a = new_state(n, dtype)
+    got = a.apply_circuit_observe(ops, q, mode=mode)
+    b = new_state(n, dtype)
+    b.apply_circuit(ops, mode=mode)
+    ref = b.observables(q)
+    a.close()
+    b.close()
+    assert got == ref
+    _check_readout(got, _readouts(sv.simulate(n, ops), n, q), n, dtype)
+
+
+def test_apply_circuit_observe_rejects_a_bad_qubit():
+    from paper_2411_15332_gb300 import _lib as L
+    n = 13
+    s = new_state(n)
+    with pytest.raises(L.MeraError) as e:
+        s.apply_circuit_observe(inputs.layered_circuit(n, 1, seed=1), n)
+    assert e.value.code == L.MERA_EINVAL
+    s.close()
